@@ -1,0 +1,429 @@
+"""Benchmark: batched FP32 C2C FFT size sweep on GB300.
+
+One step = the whole plain FFT path over the size sweep: for every N in
+{256, 512, ..., 16384}, one forward and one inverse transform of 2^25
+complex64 points (256 MiB in, 256 MiB out; batch = 2^25 / N), inputs i.i.d.
+N(0,1) from seed 0, already resident in HBM.  Every input (256 MiB) is larger
+than the 129 MB L2, so no flush is needed between timed calls.
+
+Metric: GFLOPS = sum of 5 N log2 N per transform / time (paper Sec. VI-A),
+and the fraction of HBM bandwidth at 16 N bytes per transform.
+
+Printed: ONE JSON line (rank 0).  Extra objects report the per-size numbers,
+the forward+backward spectral filter against plain transforms, and the
+oracle's CPU baseline.  ``--impl reference`` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SIZES = [256, 512, 1024, 2048, 4096, 8192, 16384]
+POINTS = 1 << 25
+METRIC = "FFT GFLOPS (5N·log2N) & % HBM peak, N=256-16384 on 1 GB300; fwd+bwd vs plain"
+WORKLOAD = ("plain FP32 C2C FFT size sweep N=256..16384, fwd+inv, 2^25 complex64 points "
+            "(256 MiB) per call, batch=2^25/N, N(0,1) seed 0")
+
+
+def flops(N: int, batch: int) -> float:
+    return 5.0 * N * math.log2(N) * batch
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2603_27569_gb300", "csrc", "*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.lines = []
+        self.proc = None
+        self.t_on = self.t_off = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-i", str(self.idx), "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark_on(self):
+        self.t_on = time.time()
+
+    def mark_off(self):
+        self.t_off = time.time()
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.lines:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        rows = []
+        for t, ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                rows.append((t, float(f[2]), float(f[3]), f[6:10]))
+            except ValueError:
+                continue
+        win = [r for r in rows if self.t_on and self.t_on <= r[0] <= (self.t_off or r[0])]
+        use = win if win else rows[-3:]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in use for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": max(r[2] for r in use),
+                "reasons": reasons, "samples": len(use), "in_window": bool(win)}
+
+
+def traffic_for(kernel_key: str):
+    """ncu DRAM bytes per launch for this kernel if captured on the current source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(kernel_key)
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline (the FP64 oracle, as it stands)
+# ---------------------------------------------------------------------------
+def oracle_sample(budget_s: float, nthreads: int):
+    """Time the oracle on rows of each (N, direction) of the sweep for about
+    budget_s / 14 seconds each; return (GFLOPS, description)."""
+    import numpy as np
+
+    import oracle
+    from paper_2603_27569_gb300 import synth
+
+    oracle.build()
+    per = budget_s / (2 * len(SIZES))
+    tot_f = tot_t = 0.0
+    rows_done = {}
+    for N in SIZES:
+        x = synth.gaussian((max(nthreads, 4) * 4, N), seed=0)
+        for inverse in (False, True):
+            t0 = time.perf_counter()
+            done = 0
+            while True:
+                r = max(nthreads, 1)
+                oracle.fft(x[:r], inverse=inverse, nthreads=nthreads)
+                done += r
+                if time.perf_counter() - t0 >= per:
+                    break
+            dt = time.perf_counter() - t0
+            tot_f += flops(N, done)
+            tot_t += dt
+            rows_done[f"{N}{'i' if inverse else 'f'}"] = done
+    desc = (f"FP64 recursive radix-2 oracle, {nthreads} threads, ~{per:.2f}s per (N, dir) "
+            f"over N=256..16384 fwd+inv; rows timed: {rows_done}")
+    return tot_f / tot_t / 1e9, desc
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    nthreads = os.cpu_count() or 1
+    # each step is a bounded sample; the whole run stays within ~2 minutes
+    budget = min(args.ref_budget, 120.0 / max(1, args.steps + args.warmup))
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(budget / 10, nthreads)
+    desc = ""
+    for _ in range(args.steps):
+        v, desc = oracle_sample(budget, nthreads)
+        vals.append(v)
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GFLOPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "points_per_call": POINTS,
+                                        "sizes": SIZES},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GFLOPS", "cores": nthreads,
+                         "kind": "oracle", "sample": desc},
+        "e2e": {"value": round(value, 4), "unit": "GFLOPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2603_27569_gb300 as fg
+    from paper_2603_27569_gb300 import build as fbuild
+    from paper_2603_27569_gb300 import synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0:
+        fbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    fg.lib()
+
+    # Inputs: one 2^25-point N(0,1) buffer (seed 0), viewed as [2^25/N, N].
+    x = torch.from_numpy(synth.gaussian(POINTS, seed=0)).to(dev)
+    y = torch.empty_like(x)
+    plans = {}
+    for N in SIZES:
+        for d in (fg.FFT_FORWARD, fg.FFT_INVERSE):
+            plans[(N, d)] = fg.Plan(N, POINTS // N, d, device=dev)
+    launches_per_exec = {k: (2 if p.info()["path"] == fg.FFT_PATH_FOURSTEP else 1)
+                         for k, p in plans.items()}
+    stream = torch.cuda.current_stream(dev)
+    keys = list(plans)
+
+    def step(ev=None):
+        for i, k in enumerate(keys):
+            if ev is not None:
+                ev[i][0].record(stream)
+            plans[k].exec(x, out=y, stream=stream)
+            if ev is not None:
+                ev[i][1].record(stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(1.0)  # let the sampler emit before the timed region
+    evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+            for _ in keys] for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.mark_on()
+    t_start.record(stream)
+    for s in range(args.steps):
+        step(evs[s])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clocks.mark_off()
+    if world > 1:
+        torch.distributed.barrier()
+    time.sleep(0.3)
+    clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    step_flops = sum(flops(N, POINTS // N) for (N, _d) in keys)
+    value = step_flops * args.steps * world / (total_ms * 1e-3) / 1e9
+
+    peak, peak_kind = peaks()
+    per_key_ms = {k: statistics.mean(evs[s][i][0].elapsed_time(evs[s][i][1])
+                                     for s in range(args.steps)) for i, k in enumerate(keys)}
+    per_size = {}
+    for N in SIZES:
+        f_ms, i_ms = per_key_ms[(N, fg.FFT_FORWARD)], per_key_ms[(N, fg.FFT_INVERSE)]
+        gbs_f = 16.0 * POINTS / (f_ms * 1e-3) / 1e9
+        gbs_i = 16.0 * POINTS / (i_ms * 1e-3) / 1e9
+        info = plans[(N, fg.FFT_FORWARD)].info()
+        per_size[str(N)] = {
+            "fwd_us": round(f_ms * 1e3, 2), "inv_us": round(i_ms * 1e3, 2),
+            "fwd_gflops": round(flops(N, POINTS // N) / (f_ms * 1e-3) / 1e9, 1),
+            "inv_gflops": round(flops(N, POINTS // N) / (i_ms * 1e-3) / 1e9, 1),
+            "fwd_frac_hbm": round(gbs_f / peak, 4), "inv_frac_hbm": round(gbs_i / peak, 4),
+            "path": {1: "single_cta", 2: "fourstep"}.get(info["path"], info["path"]),
+            "radix": info["radix"], "points_per_thread": info["points_per_thread"],
+        }
+    dom = max(keys, key=lambda k: per_key_ms[k])
+    dom_ms = per_key_ms[dom]
+    dom_info = plans[dom].info()
+    kname = (f"{'stockham' if dom_info['path'] == 1 else 'fourstep'}_N{dom[0]}_"
+             f"{'fwd' if dom[1] < 0 else 'inv'}")
+    achieved = 16.0 * POINTS / (dom_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic_for(kname),
+                "kernel": kname, "peak_source": f"{peak_kind} hbm_gbs",
+                "algorithmic_bytes_per_launch": 16 * POINTS,
+                "launch_us": round(dom_ms * 1e3, 2)}
+    total_fft_bytes = 16.0 * POINTS * len(keys)
+    overall_frac = total_fft_bytes / (ms_per_step * 1e-3) / 1e9 / peak
+    gpu_launches = sum(launches_per_exec[k] for k in keys) * args.steps
+
+    # End to end through the host-buffer entry point (pinned host memory).
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(synth.gaussian(POINTS, seed=0)).pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        for k in keys:  # warm the staging buffers
+            plans[k].exec_host(xh, yh)
+        e_steps = max(1, min(args.steps, args.e2e_steps))
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            for k in keys:
+                plans[k].exec_host(xh, yh)
+        torch.cuda.synchronize()
+        e_s = time.perf_counter() - t0
+        if world > 1:
+            tt = torch.tensor([e_s], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            e_s = float(tt.item())
+        e2e = {"value": round(step_flops * e_steps * world / e_s / 1e9, 2), "unit": "GFLOPS",
+               "h2d_bytes_per_step": 8 * POINTS * len(keys),
+               "d2h_bytes_per_step": 8 * POINTS * len(keys),
+               "steps": e_steps, "path": "fft_exec_host (pinned host buffers, chunked pipeline)"}
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras["fwd_bwd"] = bench_fwd_bwd(fg, synth, torch, dev, per_key_ms)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        nthreads = os.cpu_count() or 1
+        v, desc = oracle_sample(args.cpu_budget, nthreads)
+        cpu = {"value": round(v, 4), "unit": "GFLOPS", "cores": nthreads, "kind": "oracle",
+               "sample": desc}
+
+    clk = clocks.summary()
+    for p in plans.values():
+        p.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": "GFLOPS", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup),
+            "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "points_per_call": POINTS, "sizes": SIZES,
+                       "calls_per_step": len(keys), "l2": "inputs larger than L2 (256 MiB > 129 MB)",
+                       "parallelism": f"weak, {world} GPU(s), independent batches per rank"},
+            "frac_hbm_step": round(overall_frac, 4),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+            "clocks": clk, "per_size": per_size, "source_hash": source_hash(),
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def bench_fwd_bwd(fg, synth, torch, dev, per_key_ms):
+    """SAR spectral filter [4096, 8192]: forward + backward vs 4 plain FFTs."""
+    rows, N = 4096, 8192
+    x_np, pulse = synth.sar_echoes(rows, N, Np=2048, seed=0)
+    x = torch.from_numpy(x_np).to(dev).requires_grad_(True)
+    Hp = fg.fft(torch.from_numpy(pulse).to(dev).reshape(1, N)).reshape(N).conj()
+    layer = fg.SpectralFilter(Hp)
+    m = torch.from_numpy(synth.real_mask((rows, N), seed=2)).to(dev)
+
+    def once():
+        x.grad = None
+        layer.H.grad = None
+        y = layer(x)
+        y.backward((2.0 * m * y).detach())   # dL/dy for L = sum m |y|^2
+        return y
+
+    for _ in range(3):
+        once()
+    torch.cuda.synchronize()
+    reps = 10
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        once()
+    b.record()
+    torch.cuda.synchronize()
+    fb_ms = a.elapsed_time(b) / reps
+    plain_ms = per_key_ms[(N, fg.FFT_FORWARD)] * rows * N / POINTS
+    plain4 = 4 * plain_ms
+    return {"workload": "spectral filter y=IFFT(FFT(x)*H), x [4096, 8192] chirp echoes, "
+                        "loss grad 2 m y; fwd+bwd incl. grad_x and grad_H",
+            "fwd_bwd_ms": round(fb_ms, 4), "plain_fft_ms": round(plain_ms, 4),
+            "ratio_vs_4_plain": round(fb_ms / plain4, 3),
+            "gflops_equiv": round(4 * flops(N, rows) / (fb_ms * 1e-3) / 1e9, 1)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-budget", type=float, default=8.0)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,252 @@
+/*
+ * fftgb — batched single-precision complex-to-complex FFT for GB300 (sm_103a).
+ *
+ * C ABI of libfftgb.so.  Plain pointers and sizes only; no C++ or framework
+ * types cross this boundary.
+ *
+ * The transform (paper Sec. II-A): for each of `batch` transforms of length N,
+ *     forward  X[k] = sum_{n=0}^{N-1} x[n] W_N^{n k},   W_N = exp(-2 pi i / N),
+ *              unnormalised;
+ *     inverse  x[n] = (1/N) sum_k X[k] exp(+2 pi i n k / N)
+ *              (the paper defines only the forward transform; the inverse is
+ *               scaled by 1/N unless FFT_FLAG_UNNORMALIZED_INVERSE is given).
+ * It is computed as a Stockham autosort factorisation (Sec. II-B) with
+ * register-resident radix-8/16 DIT butterflies and radix-4/2 tails
+ * (Sec. V-A, V-B), shared-memory exchange between passes, precomputed
+ * twiddle tables, and a four-step decomposition (Sec. IV-B, Eq. 2) for large N.
+ *
+ * Data layout (all entry points unless stated otherwise): interleaved complex
+ * float32 (`float2`: re, im), transform-major: element n of transform b is at
+ * index b*N + n.  Device buffers are owned by the caller, must be 16-byte
+ * aligned, and must not overlap partially; in == out (in place) is allowed.
+ *
+ * Asynchrony: every exec call enqueues work on the caller's CUDA stream
+ * (`stream` is a cudaStream_t; NULL means the legacy default stream) and
+ * returns without synchronising.  Errors detected on the host are returned
+ * immediately; errors raised by kernels are recorded in a per-plan device
+ * status word read by fft_last_device_status() after a synchronisation.
+ *
+ * Thread safety: a plan may be executed from one host thread at a time;
+ * different plans are independent.
+ */
+#ifndef FFTGB_H_
+#define FFTGB_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fft_plan_s *fft_plan_t;
+
+/* The value is the sign of the exponent of the transform kernel. */
+typedef enum { FFT_FORWARD = -1, FFT_INVERSE = 1 } fft_direction_t;
+
+typedef enum {
+    FFT_PREC_FP32 = 0,    /* FP32 data and arithmetic (the plain path)        */
+    FFT_PREC_FP16X2 = 1,  /* tensor-core radix-16 DFT, FP16 hi+lo operands     */
+    FFT_PREC_BF16X2 = 2   /* tensor-core radix-16 DFT, BF16 hi+lo operands     */
+} fft_precision_t;
+
+typedef enum {
+    FFT_OK = 0,
+    FFT_ERR_INVALID_SIZE = 1,   /* N not a supported power of two, batch < 0   */
+    FFT_ERR_INVALID_VALUE = 2,  /* bad handle, direction, flag or overlap      */
+    FFT_ERR_MISALIGNED = 3,     /* a pointer is not 16-byte aligned            */
+    FFT_ERR_ALLOC = 4,          /* device or host allocation failed            */
+    FFT_ERR_CUDA = 5,           /* a CUDA runtime call failed                  */
+    FFT_ERR_TIMEOUT = 6,        /* a bounded device-side wait ran out          */
+    FFT_ERR_NOT_SUPPORTED = 7   /* valid request this build does not implement */
+} fft_status_t;
+
+/* Plan flags (bitwise OR). */
+#define FFT_FLAG_UNNORMALIZED_INVERSE 0x1 /* inverse without the 1/N factor    */
+#define FFT_FLAG_FORCE_SINGLE_CTA 0x2     /* whole transform inside one CTA    */
+#define FFT_FLAG_FORCE_FOURSTEP 0x4       /* two-phase four-step through L2/HBM */
+#define FFT_FLAG_NO_AUTOTUNE_CACHE 0x8    /* ignore the autotuner's choices     */
+/* Plan the ADJOINT of the `direction` transform instead of the transform:
+ * adjoint(forward F) = F^H, the unnormalised conjugate-sign transform;
+ * adjoint(inverse G = F^H / N) = F / N.  The backward pass of a layer that
+ * applies F (or G) applies this plan to the incoming gradient. */
+#define FFT_FLAG_ADJOINT 0x10
+
+/* Execution paths reported by fft_plan_info(). */
+#define FFT_PATH_SINGLE_CTA 1  /* Stockham, every pass inside one CTA        */
+#define FFT_PATH_FOURSTEP 2    /* column FFTs + twiddle, then row FFTs        */
+#define FFT_PATH_RAGGED 3      /* persistent ragged launch                    */
+#define FFT_PATH_TENSORCORE 4  /* split-precision tensor-core radix-16 DFT    */
+
+/* What a plan chose; filled by fft_plan_info(). */
+typedef struct {
+    int N;            /* transform length (0 for a ragged plan)                */
+    int64_t batch;    /* transforms per exec (count for a ragged plan)         */
+    int direction;    /* FFT_FORWARD / FFT_INVERSE (0 = mixed, ragged)         */
+    int precision;    /* fft_precision_t                                       */
+    int path;         /* FFT_PATH_*                                            */
+    int points_per_thread;  /* registers of complex data per thread per pass  */
+    int transforms_per_cta; /* transforms sharing one CTA (single-CTA path)   */
+    int threads_per_cta;
+    int num_passes;         /* exchange passes of the (first) kernel          */
+    int radix[8];           /* radix of each pass, first pass first           */
+    int n1, n2;             /* four-step split N = n1 * n2 (0 otherwise)       */
+    int64_t scratch_bytes;  /* device scratch owned by the plan               */
+} fft_plan_info_t;
+
+/* One compiled execution configuration (see fft_list_configs). */
+typedef struct {
+    int path;               /* FFT_PATH_SINGLE_CTA or FFT_PATH_FOURSTEP          */
+    int points_per_thread;  /* complex points each thread keeps in registers    */
+    int transforms_per_cta; /* rows per CTA (single-CTA path)                    */
+    int threads_per_cta;
+    int num_passes;
+    int radix[8];           /* radix schedule of the (first) kernel              */
+    int n1;                 /* four-step: N = n1 * (N / n1); 0 otherwise         */
+} fft_config_t;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *fft_status_string(fft_status_t status);
+
+/*
+ * fft_plan — plan `batch` transforms of length N in one direction.
+ * N: power of two, 2 <= N <= 16384.  batch >= 0 (0 makes a valid plan whose
+ * exec does nothing).  direction: FFT_FORWARD or FFT_INVERSE.
+ * Allocates and fills the plan's twiddle tables on the current device
+ * (generated in FP64 on the GPU, rounded to FP32) and synchronises once.
+ * On success *out holds a plan to free with fft_destroy(); on failure *out is
+ * set to NULL.
+ * Paper: Sec. IV-D (synthesis rules) decides the factorisation; the
+ * radix schedule follows Sec. V-B/V-D.
+ */
+fft_status_t fft_plan(fft_plan_t *out, int N, int64_t batch, int direction);
+
+/* As fft_plan with a precision (fft_precision_t) and FFT_FLAG_* flags.
+ * The tensor-core precisions support N in {256, 4096, 16384} only
+ * (FFT_ERR_NOT_SUPPORTED otherwise). */
+fft_status_t fft_plan_ex(fft_plan_t *out, int N, int64_t batch, int direction,
+                         int precision, int flags);
+
+/*
+ * fft_list_configs — enumerate the FP32 execution configurations compiled
+ * into this library for length N: every single-CTA Stockham variant (radix
+ * schedule, points per thread, transforms per CTA) and every four-step split.
+ * Writes min(count, capacity) entries to out (out may be NULL) and returns
+ * the total count (0 for an unsupported N).
+ */
+int fft_list_configs(int N, fft_config_t *out, int capacity);
+
+/*
+ * fft_plan_config — plan with one explicit configuration from
+ * fft_list_configs (used by the autotuner and by tests that cover every
+ * configuration).  flags as in fft_plan_ex, except the FORCE_* flags.
+ * FFT_ERR_NOT_SUPPORTED if the configuration is not compiled in.
+ */
+fft_status_t fft_plan_config(fft_plan_t *out, int N, int64_t batch, int direction,
+                             int flags, const fft_config_t *config);
+
+/*
+ * fft_exec — run the plan on device buffers.
+ * in, out: device pointers to batch*N float2 each (see layout above), 16-byte
+ * aligned; in == out is allowed, partial overlap is FFT_ERR_INVALID_VALUE.
+ * For a ragged plan, in and out are the packed base pointers the plan's
+ * offsets index.  stream: cudaStream_t or NULL.  Asynchronous.
+ */
+fft_status_t fft_exec(fft_plan_t plan, const void *in, void *out, void *stream);
+
+/*
+ * fft_exec_host — the same transform on HOST buffers: the library copies the
+ * input to device memory it owns, runs the plan and copies the result back,
+ * pipelining the copies with the transforms in chunks.  Blocks until the
+ * result is in host_out.  Page-locked (pinned) host memory gives full copy
+ * bandwidth; pageable memory works but is slower.  Not for ragged plans.
+ */
+fft_status_t fft_exec_host(fft_plan_t plan, const void *host_in, void *host_out,
+                           void *stream);
+
+/* Free a plan and all device memory it owns.  NULL is accepted. */
+fft_status_t fft_destroy(fft_plan_t plan);
+
+/* Describe what a plan chose (path, radix schedule, threads, split). */
+fft_status_t fft_plan_info(fft_plan_t plan, fft_plan_info_t *info);
+
+/*
+ * Read and clear the plan's device status word.  Synchronises the device.
+ * Returns FFT_OK, or the first error a kernel recorded (FFT_ERR_TIMEOUT for a
+ * bounded wait that ran out).
+ */
+fft_status_t fft_last_device_status(fft_plan_t plan);
+
+/*
+ * fft_twiddle_table — copy the plan's FP32 twiddle table to host memory
+ * (for inspection and tests).  *count receives the number of complex entries;
+ * if host_out is non-NULL, min(*count, capacity) entries are copied.
+ * Each entry is W_M^e = exp(-2 pi i e / M) for the (M, e) that
+ * fft_twiddle_index() reports for the same position.
+ */
+fft_status_t fft_twiddle_table(fft_plan_t plan, void *host_out, int64_t capacity,
+                               int64_t *count);
+/* Position -> (M, e) of the twiddle table entry. */
+fft_status_t fft_twiddle_index(fft_plan_t plan, int64_t pos, int64_t *M, int64_t *e);
+
+/*
+ * fft_ragged_plan — a batch of `count` transforms of mixed lengths and
+ * directions, executed in ONE persistent launch (longest transforms first,
+ * work claimed through a device counter).
+ * N[i]: power of two in [2, 16384]; direction[i]: -1 or +1;
+ * in_offset[i], out_offset[i]: start of transform i, in complex elements,
+ * inside the packed buffers passed to fft_exec(); every offset must be a
+ * multiple of 2 (16-byte alignment).  Host arrays are copied; the caller keeps
+ * ownership.  flags: FFT_FLAG_UNNORMALIZED_INVERSE and
+ * FFT_FLAG_NO_AUTOTUNE_CACHE are honoured.
+ */
+fft_status_t fft_ragged_plan(fft_plan_t *out, int count, const int *N,
+                             const int *direction, const int64_t *in_offset,
+                             const int64_t *out_offset, int flags);
+
+/*
+ * fft_autotune — time the candidate configurations (points per thread, radix
+ * schedule, transforms per CTA, single-CTA vs four-step) for (N, direction,
+ * precision) on the current device with a batch of `batch` transforms, and
+ * store the fastest in the process-wide cache used by later plans.  If
+ * cache_path is non-NULL the whole cache is also written there as JSON
+ * (keyed by GPU name, N, direction, precision).  Allocates its own buffers.
+ */
+fft_status_t fft_autotune(int N, int direction, int precision, int64_t batch,
+                          const char *cache_path);
+/* Load a JSON cache written by fft_autotune (entries for other GPUs are
+ * ignored).  A missing file is FFT_ERR_INVALID_VALUE. */
+fft_status_t fft_autotune_load(const char *cache_path);
+/* Forget every autotuned choice (plans fall back to the built-in table). */
+fft_status_t fft_autotune_clear(void);
+
+/*
+ * Spectral-filter building blocks (SAR range compression, paper Sec. II-D and
+ * the fused pipeline of Sec. IX-A), for y = IFFT(FFT(x) * H).
+ *
+ * fft_filter_apply: Z[b][k] = X[b][k] * H[k] (conj_h = 0) or
+ *   X[b][k] * conj(H[k]) (conj_h = 1), elementwise, for batch rows of N
+ *   points; Z may alias X.  scale multiplies the result (exact for powers of 2).
+ * fft_filter_grad_h: grad_H[k] = sum_b conj(X[b][k]) * G[b][k], accumulated in
+ *   FP32 with a fixed-order tree (bitwise reproducible).  Uses the plan-free
+ *   scratch `work` of fft_filter_grad_h_workspace(N, batch) bytes.
+ * fft_spectral_filter_fused: one kernel per row doing forward FFT, multiply
+ *   by H (or conj H) and inverse FFT in shared memory (one HBM round trip);
+ *   direction of the outer transform pair given by `adjoint` (0: y =
+ *   IFFT(FFT(x) H); 1: y = FFT-adjoint pair used by the backward pass,
+ *   g = (1/N) FFT(g_y) * conj(H) then F^H).  N in [256, 16384].
+ * All pointers are device pointers, 16-byte aligned; asynchronous on stream.
+ */
+fft_status_t fft_filter_apply(const void *X, const void *H, void *Z, int N,
+                              int64_t batch, int conj_h, float scale, void *stream);
+int64_t fft_filter_grad_h_workspace(int N, int64_t batch);
+fft_status_t fft_filter_grad_h(const void *X, const void *G, void *grad_H, int N,
+                               int64_t batch, void *work, void *stream);
+fft_status_t fft_spectral_filter_fused(const void *x, const void *H, void *y, int N,
+                                       int64_t batch, int adjoint, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFTGB_H_ */

@@ -1,0 +1,635 @@
+// C ABI of libfftgb: planning, twiddle generation and execution.
+//
+// Planning follows the synthesis rules of the paper (Sec. IV-D) re-derived
+// for GB300: a transform whose N points fit one CTA's shared memory (every N
+// up to 16384 = 128 KiB, within the 227 KiB a CTA may use) runs as a
+// single-CTA Stockham kernel; the two-phase four-step path (Sec. IV-B,
+// Eq. 2) splits N = N1 N2 into column FFTs plus twiddle, then row FFTs,
+// through a device intermediate.  The autotuner's cache may override either
+// choice per (N, direction, precision).
+//
+// Twiddle tables (Sec. V-A/V-B compute them with a sincos chain; here they are
+// precomputed once per plan): every entry W_M^e = exp(-2 pi i e / M) is
+// formed on the GPU in FP64 with sincospi(-2 e / M) from the exact integer e,
+// then rounded to nearest FP32.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "column.cuh"
+#include "plan.h"
+
+namespace fftgb {
+
+// ---------------------------------------------------------------------------
+// Registry
+// ---------------------------------------------------------------------------
+static std::vector<KernelEntry> &registry_storage() {
+  static std::vector<KernelEntry> v;
+  return v;
+}
+void register_kernel(const KernelEntry &e) { registry_storage().push_back(e); }
+const std::vector<KernelEntry> &kernel_registry() { return registry_storage(); }
+
+const KernelEntry *find_stockham(int N, int P, int TB, const int *radix, int npass) {
+  for (const auto &e : kernel_registry()) {
+    if (e.kind != KIND_STOCKHAM || e.N != N || e.P != P || e.TB != TB || e.npass != npass) continue;
+    bool same = true;
+    for (int i = 0; i < npass; ++i) same = same && e.radix[i] == radix[i];
+    if (same) return &e;
+  }
+  return nullptr;
+}
+
+const KernelEntry *default_stockham(int N) {
+  const KernelEntry *any = nullptr;
+  for (const auto &e : kernel_registry()) {
+    if (e.kind != KIND_STOCKHAM || e.N != N) continue;
+    if (e.is_default) return &e;
+    if (!any) any = &e;
+  }
+  return any;
+}
+
+const KernelEntry *default_column(int L, int variant) {
+  for (const auto &e : kernel_registry())
+    if (e.kind == KIND_COLUMN && e.N == L && e.variant == variant && e.is_default) return &e;
+  return nullptr;
+}
+
+fft_status_t cuda_status(cudaError_t e) { return e == cudaSuccess ? FFT_OK : FFT_ERR_CUDA; }
+
+#define FFTGB_CUDA(call)                                  \
+  do {                                                    \
+    cudaError_t err__ = (call);                           \
+    if (err__ != cudaSuccess) return FFT_ERR_CUDA;        \
+  } while (0)
+
+fft_status_t ensure_smem_attr(const KernelEntry *k) {
+  if (k->smem > 48 * 1024) {
+    for (int d = 0; d < 2; ++d)
+      FFTGB_CUDA(cudaFuncSetAttribute(k->fn[d], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)k->smem));
+  }
+  return FFT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Twiddle generation (FP64 on the GPU, rounded to FP32)
+// ---------------------------------------------------------------------------
+// Pass table: entry (j - 1) * p + k = W_{p r}^{j k}, 1 <= j < r, 0 <= k < p.
+__global__ void gen_pass_twiddles(float2 *out, int p, int r) {
+  const int64_t total = (int64_t)(r - 1) * p;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int64_t j = idx / p + 1, k = idx % p;
+  const int64_t M = (int64_t)p * r;
+  const int64_t e = (j * k) % M;
+  double s, c;
+  sincospi(-2.0 * (double)e / (double)M, &s, &c);
+  out[idx] = make_float2(__double2float_rn(c), __double2float_rn(s));
+}
+
+// Full table: entry e = W_M^e, 0 <= e < M.
+__global__ void gen_full_twiddles(float2 *out, int64_t M) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M) return;
+  double s, c;
+  sincospi(-2.0 * (double)e / (double)M, &s, &c);
+  out[e] = make_float2(__double2float_rn(c), __double2float_rn(s));
+}
+
+std::vector<TwSeg> pass_segments(const KernelEntry &k, int64_t &offset) {
+  std::vector<TwSeg> segs;
+  int p = k.radix[0];
+  for (int s = 1; s < k.npass; ++s) {
+    TwSeg g;
+    g.offset = offset;
+    g.count = (int64_t)(k.radix[s] - 1) * p;
+    g.kind = 0;
+    g.p = p;
+    g.r = k.radix[s];
+    g.M = (int64_t)p * k.radix[s];
+    offset += g.count;
+    segs.push_back(g);
+    p *= k.radix[s];
+  }
+  return segs;
+}
+
+fft_status_t build_twiddles(fft_plan_impl *pl, const std::vector<TwSeg> &segs) {
+  int64_t total = 0;
+  for (const auto &g : segs) total = std::max(total, g.offset + g.count);
+  pl->tw_segs = segs;
+  pl->tw_count = total;
+  if (total == 0) return FFT_OK;
+  if (cudaMalloc(&pl->d_tw, sizeof(float2) * (size_t)total) != cudaSuccess) {
+    cudaGetLastError();
+    return FFT_ERR_ALLOC;
+  }
+  for (const auto &g : segs) {
+    if (g.count == 0) continue;
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((g.count + threads - 1) / threads);
+    if (g.kind == 0)
+      gen_pass_twiddles<<<blocks, threads>>>(pl->d_tw + g.offset, g.p, g.r);
+    else
+      gen_full_twiddles<<<blocks, threads>>>(pl->d_tw + g.offset, g.M);
+    FFTGB_CUDA(cudaGetLastError());
+  }
+  FFTGB_CUDA(cudaDeviceSynchronize());
+  return FFT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Launch helpers
+// ---------------------------------------------------------------------------
+fft_status_t launch_stockham(const KernelEntry *k, int dir, const float2 *in, float2 *out,
+                             const float2 *tw, int64_t rows, float scale, cudaStream_t st) {
+  if (rows <= 0) return FFT_OK;
+  StockhamArgs a;
+  a.in = in;
+  a.out = out;
+  a.tw = tw;
+  a.batch = rows;
+  a.scale = scale;
+  const int64_t grid = (rows + k->TB - 1) / k->TB;
+  if (grid > 0x7fffffffLL) return FFT_ERR_INVALID_SIZE;
+  void *args[] = {&a};
+  FFTGB_CUDA(cudaLaunchKernel(k->fn[dir > 0 ? 1 : 0], dim3((unsigned)grid), dim3(k->threads),
+                              args, k->smem, st));
+  return FFT_OK;
+}
+
+static fft_status_t launch_column(const KernelEntry *k, int dir, const ColumnArgs &ca,
+                                  cudaStream_t st) {
+  const int64_t grid = ca.nmat * (ca.ncols / k->TB);
+  if (grid <= 0) return FFT_OK;
+  if (grid > 0x7fffffffLL) return FFT_ERR_INVALID_SIZE;
+  ColumnArgs a = ca;
+  void *args[] = {&a};
+  FFTGB_CUDA(cudaLaunchKernel(k->fn[dir > 0 ? 1 : 0], dim3((unsigned)grid), dim3(k->threads),
+                              args, k->smem, st));
+  return FFT_OK;
+}
+
+fft_status_t exec_rows(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t rows,
+                       cudaStream_t st) {
+  if (rows <= 0) return FFT_OK;
+  if (pl->path == FFT_PATH_SINGLE_CTA) {
+    return launch_stockham(pl->k_single, pl->direction, in, out, pl->d_tw + pl->tw_single, rows,
+                           pl->scale, st);
+  }
+  if (pl->path == FFT_PATH_FOURSTEP) {
+    ColumnArgs c1{};
+    c1.in = in;
+    c1.out = pl->d_scratch;
+    c1.tw = pl->d_tw + pl->tw_col1;
+    c1.tw_big = pl->d_tw + pl->tw_big;
+    c1.nmat = rows;
+    c1.in_mat_stride = pl->N;
+    c1.out_mat_stride = pl->N;
+    c1.in_row_stride = pl->n1;
+    c1.out_row_stride = 0;
+    c1.ncols = pl->n1;
+    c1.ntot = pl->N;
+    c1.scale = 1.f;
+    fft_status_t s = launch_column(pl->k_col1, pl->direction, c1, st);
+    if (s != FFT_OK) return s;
+    ColumnArgs c2{};
+    c2.in = pl->d_scratch;
+    c2.out = out;
+    c2.tw = pl->d_tw + pl->tw_col2;
+    c2.tw_big = nullptr;
+    c2.nmat = rows;
+    c2.in_mat_stride = pl->N;
+    c2.out_mat_stride = pl->N;
+    c2.in_row_stride = pl->n2;
+    c2.out_row_stride = pl->n2;
+    c2.ncols = pl->n2;
+    c2.ntot = pl->N;
+    c2.scale = pl->scale;
+    return launch_column(pl->k_col2, pl->direction, c2, st);
+  }
+  if (pl->path == FFT_PATH_TENSORCORE) return tc_exec(pl, in, out, rows, st);
+  return FFT_ERR_INVALID_VALUE;
+}
+
+static bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Four-step split N = n1 * n2 with both factors column-kernel lengths (16..256).
+static bool fourstep_split(int N, int want_n1, int *n1, int *n2) {
+  auto ok = [&](int a) {
+    int b = N / a;
+    return a >= 16 && b >= 16 && a <= 256 && b <= 256 && default_column(b, 1) && default_column(a, 0);
+  };
+  if (want_n1 > 0) {
+    if (N % want_n1 || !ok(want_n1)) return false;
+    *n1 = want_n1;
+    *n2 = N / want_n1;
+    return true;
+  }
+  // Prefer n2 >= n1 (longer first-phase transforms), as square as possible.
+  int best = 0;
+  for (int a = 16; a <= 256; a *= 2)
+    if (N % a == 0 && ok(a) && a <= N / a) best = a;
+  if (!best) return false;
+  *n1 = best;
+  *n2 = N / best;
+  return true;
+}
+
+static fft_status_t plan_fourstep(fft_plan_impl *pl, int want_n1) {
+  int n1, n2;
+  if (!fourstep_split(pl->N, want_n1, &n1, &n2)) return FFT_ERR_NOT_SUPPORTED;
+  pl->path = FFT_PATH_FOURSTEP;
+  pl->n1 = n1;
+  pl->n2 = n2;
+  pl->k_col1 = default_column(n2, 1);
+  pl->k_col2 = default_column(n1, 0);
+  fft_status_t s = ensure_smem_attr(pl->k_col1);
+  if (s == FFT_OK) s = ensure_smem_attr(pl->k_col2);
+  if (s != FFT_OK) return s;
+  int64_t off = 0;
+  std::vector<TwSeg> segs;
+  pl->tw_col1 = off;
+  auto a = pass_segments(*pl->k_col1, off);
+  segs.insert(segs.end(), a.begin(), a.end());
+  pl->tw_col2 = off;
+  auto b = pass_segments(*pl->k_col2, off);
+  segs.insert(segs.end(), b.begin(), b.end());
+  pl->tw_big = off;
+  TwSeg big;
+  big.offset = off;
+  big.count = pl->N;
+  big.kind = 1;
+  big.p = big.r = 0;
+  big.M = pl->N;
+  off += pl->N;
+  segs.push_back(big);
+  s = build_twiddles(pl, segs);
+  if (s != FFT_OK) return s;
+  pl->scratch_bytes = (int64_t)sizeof(float2) * pl->N * pl->batch;
+  if (pl->scratch_bytes > 0) {
+    if (cudaMalloc(&pl->d_scratch, (size_t)pl->scratch_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return FFT_ERR_ALLOC;
+    }
+  }
+  return FFT_OK;
+}
+
+static fft_status_t plan_single(fft_plan_impl *pl, const KernelEntry *k) {
+  if (!k) return FFT_ERR_NOT_SUPPORTED;
+  pl->path = FFT_PATH_SINGLE_CTA;
+  pl->k_single = k;
+  fft_status_t s = ensure_smem_attr(k);
+  if (s != FFT_OK) return s;
+  int64_t off = 0;
+  pl->tw_single = 0;
+  auto segs = pass_segments(*k, off);
+  return build_twiddles(pl, segs);
+}
+
+static void free_plan(fft_plan_impl *pl) {
+  if (!pl) return;
+  if (pl->ragged) ragged_destroy(pl);
+  if (pl->tc) tc_destroy(pl);
+  if (pl->d_tw) cudaFree(pl->d_tw);
+  if (pl->d_scratch) cudaFree(pl->d_scratch);
+  if (pl->d_status) cudaFree(pl->d_status);
+  if (pl->d_stage) cudaFree(pl->d_stage);
+  if (pl->s_h2d) cudaStreamDestroy(pl->s_h2d);
+  if (pl->s_d2h) cudaStreamDestroy(pl->s_d2h);
+}
+
+}  // namespace fftgb
+
+using namespace fftgb;
+
+extern "C" {
+
+const char *fft_status_string(fft_status_t s) {
+  switch (s) {
+    case FFT_OK: return "FFT_OK";
+    case FFT_ERR_INVALID_SIZE: return "FFT_ERR_INVALID_SIZE";
+    case FFT_ERR_INVALID_VALUE: return "FFT_ERR_INVALID_VALUE";
+    case FFT_ERR_MISALIGNED: return "FFT_ERR_MISALIGNED";
+    case FFT_ERR_ALLOC: return "FFT_ERR_ALLOC";
+    case FFT_ERR_CUDA: return "FFT_ERR_CUDA";
+    case FFT_ERR_TIMEOUT: return "FFT_ERR_TIMEOUT";
+    case FFT_ERR_NOT_SUPPORTED: return "FFT_ERR_NOT_SUPPORTED";
+  }
+  return "FFT_ERR_UNKNOWN";
+}
+
+static fft_status_t plan_common(fft_plan_t *out, int N, int64_t batch, int direction,
+                                int precision, int flags, const fft_config_t *cfg) {
+  if (!out) return FFT_ERR_INVALID_VALUE;
+  *out = nullptr;
+  if (!is_pow2(N) || N < 2 || N > 16384 || batch < 0) return FFT_ERR_INVALID_SIZE;
+  if (direction != FFT_FORWARD && direction != FFT_INVERSE) return FFT_ERR_INVALID_VALUE;
+  if (precision < FFT_PREC_FP32 || precision > FFT_PREC_BF16X2) return FFT_ERR_INVALID_VALUE;
+  if (flags & ~(FFT_FLAG_UNNORMALIZED_INVERSE | FFT_FLAG_FORCE_SINGLE_CTA |
+                FFT_FLAG_FORCE_FOURSTEP | FFT_FLAG_NO_AUTOTUNE_CACHE | FFT_FLAG_ADJOINT))
+    return FFT_ERR_INVALID_VALUE;
+  if ((flags & FFT_FLAG_FORCE_SINGLE_CTA) && (flags & FFT_FLAG_FORCE_FOURSTEP))
+    return FFT_ERR_INVALID_VALUE;
+  fft_plan_s *h = new (std::nothrow) fft_plan_s;
+  if (!h) return FFT_ERR_ALLOC;
+  fft_plan_impl *pl = &h->impl;
+  pl->N = N;
+  pl->batch = batch;
+  pl->precision = precision;
+  pl->flags = flags;
+  {
+    // Kernel direction and output scale.  The adjoint of F is F^H (sign +1,
+    // scale 1); the adjoint of G = F^H / N is F / N (sign -1, scale 1/N).
+    const bool scaled_inverse = !(flags & FFT_FLAG_UNNORMALIZED_INVERSE);
+    if (flags & FFT_FLAG_ADJOINT) {
+      pl->direction = -direction;
+      pl->scale = (direction == FFT_INVERSE && scaled_inverse) ? 1.0f / (float)N : 1.0f;
+    } else {
+      pl->direction = direction;
+      pl->scale = (direction == FFT_INVERSE && scaled_inverse) ? 1.0f / (float)N : 1.0f;
+    }
+  }
+  cudaGetDevice(&pl->device);
+  fft_status_t s = FFT_OK;
+  if (cudaMalloc(&pl->d_status, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    s = FFT_ERR_ALLOC;
+  } else if (cudaMemset(pl->d_status, 0, sizeof(int)) != cudaSuccess) {
+    s = FFT_ERR_CUDA;
+  }
+  if (s == FFT_OK) {
+    if (cfg) {
+      if (cfg->path == FFT_PATH_FOURSTEP) {
+        s = plan_fourstep(pl, cfg->n1);
+      } else if (cfg->path == FFT_PATH_SINGLE_CTA) {
+        const KernelEntry *k = find_stockham(N, cfg->points_per_thread, cfg->transforms_per_cta,
+                                             cfg->radix, cfg->num_passes);
+        s = k ? plan_single(pl, k) : FFT_ERR_NOT_SUPPORTED;
+      } else {
+        s = FFT_ERR_INVALID_VALUE;
+      }
+    } else if (precision != FFT_PREC_FP32) {
+      s = tc_plan(pl);
+    } else if (flags & FFT_FLAG_FORCE_FOURSTEP) {
+      s = plan_fourstep(pl, 0);
+    } else if (flags & FFT_FLAG_FORCE_SINGLE_CTA) {
+      s = plan_single(pl, default_stockham(N));
+    } else {
+      TuneChoice tc;
+      bool have = !(flags & FFT_FLAG_NO_AUTOTUNE_CACHE) &&
+                  tune_lookup(N, pl->direction, precision, &tc);
+      if (have && tc.path == FFT_PATH_FOURSTEP) {
+        s = plan_fourstep(pl, tc.n1);
+        if (s == FFT_ERR_NOT_SUPPORTED) have = false;
+      } else if (have) {
+        const KernelEntry *k = find_stockham(N, tc.P, tc.TB, tc.radix, tc.npass);
+        if (k) s = plan_single(pl, k);
+        else have = false;
+      }
+      if (!have) s = plan_single(pl, default_stockham(N));
+    }
+  }
+  if (s != FFT_OK) {
+    free_plan(pl);
+    delete h;
+    return s;
+  }
+  *out = h;
+  return FFT_OK;
+}
+
+fft_status_t fft_plan_ex(fft_plan_t *out, int N, int64_t batch, int direction, int precision,
+                         int flags) {
+  return plan_common(out, N, batch, direction, precision, flags, nullptr);
+}
+
+fft_status_t fft_plan(fft_plan_t *out, int N, int64_t batch, int direction) {
+  return plan_common(out, N, batch, direction, FFT_PREC_FP32, 0, nullptr);
+}
+
+fft_status_t fft_plan_config(fft_plan_t *out, int N, int64_t batch, int direction, int flags,
+                             const fft_config_t *config) {
+  if (out) *out = nullptr;
+  if (!config) return FFT_ERR_INVALID_VALUE;
+  if (flags & (FFT_FLAG_FORCE_SINGLE_CTA | FFT_FLAG_FORCE_FOURSTEP)) return FFT_ERR_INVALID_VALUE;
+  return plan_common(out, N, batch, direction, FFT_PREC_FP32, flags, config);
+}
+
+int fft_list_configs(int N, fft_config_t *out, int capacity) {
+  int n = 0;
+  auto emit = [&](const fft_config_t &c) {
+    if (out && n < capacity) out[n] = c;
+    ++n;
+  };
+  if (!is_pow2(N) || N < 2 || N > 16384) return 0;
+  for (const auto &e : kernel_registry()) {
+    if (e.kind != KIND_STOCKHAM || e.N != N) continue;
+    fft_config_t c;
+    memset(&c, 0, sizeof(c));
+    c.path = FFT_PATH_SINGLE_CTA;
+    c.points_per_thread = e.P;
+    c.transforms_per_cta = e.TB;
+    c.threads_per_cta = e.threads;
+    c.num_passes = e.npass;
+    for (int i = 0; i < 8; ++i) c.radix[i] = e.radix[i];
+    emit(c);
+  }
+  for (int a = 16; a <= 256; a *= 2) {
+    int n1, n2;
+    if (N % a || !fourstep_split(N, a, &n1, &n2)) continue;
+    const KernelEntry *k = default_column(n2, 1);
+    fft_config_t c;
+    memset(&c, 0, sizeof(c));
+    c.path = FFT_PATH_FOURSTEP;
+    c.points_per_thread = k->P;
+    c.transforms_per_cta = k->TB;
+    c.threads_per_cta = k->threads;
+    c.num_passes = k->npass;
+    for (int i = 0; i < 8; ++i) c.radix[i] = k->radix[i];
+    c.n1 = n1;
+    emit(c);
+  }
+  return n;
+}
+
+static fft_status_t check_buffers(const void *in, const void *out, int64_t bytes) {
+  if (!in || !out) return FFT_ERR_INVALID_VALUE;
+  if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return FFT_ERR_MISALIGNED;
+  if (in != out) {
+    const char *a = (const char *)in, *b = (const char *)out;
+    if (a < b + bytes && b < a + bytes) return FFT_ERR_INVALID_VALUE;
+  }
+  return FFT_OK;
+}
+
+fft_status_t fft_exec(fft_plan_t plan, const void *in, void *out, void *stream) {
+  if (!plan) return FFT_ERR_INVALID_VALUE;
+  fft_plan_impl *pl = &plan->impl;
+  if (pl->path == FFT_PATH_RAGGED) {
+    if (!in || !out) return FFT_ERR_INVALID_VALUE;
+    if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return FFT_ERR_MISALIGNED;
+    return ragged_exec(pl, (const float2 *)in, (float2 *)out, (cudaStream_t)stream);
+  }
+  if (pl->batch == 0) return FFT_OK;
+  fft_status_t s = check_buffers(in, out, (int64_t)sizeof(float2) * pl->N * pl->batch);
+  if (s != FFT_OK) return s;
+  return exec_rows(pl, (const float2 *)in, (float2 *)out, pl->batch, (cudaStream_t)stream);
+}
+
+fft_status_t fft_exec_host(fft_plan_t plan, const void *host_in, void *host_out, void *stream) {
+  if (!plan) return FFT_ERR_INVALID_VALUE;
+  fft_plan_impl *pl = &plan->impl;
+  if (pl->path == FFT_PATH_RAGGED) return FFT_ERR_NOT_SUPPORTED;
+  if (pl->batch == 0) return FFT_OK;
+  if (!host_in || !host_out) return FFT_ERR_INVALID_VALUE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t row_bytes = (int64_t)sizeof(float2) * pl->N;
+  // Chunks of about 32 MiB; two input and two output staging slots.
+  if (!pl->d_stage) {
+    int64_t rows = std::max<int64_t>(1, (32ll << 20) / row_bytes);
+    rows = std::min(rows, pl->batch);
+    if (cudaMalloc(&pl->d_stage, (size_t)(4 * rows * row_bytes)) != cudaSuccess) {
+      cudaGetLastError();
+      return FFT_ERR_ALLOC;
+    }
+    pl->stage_rows = rows;
+    FFTGB_CUDA(cudaStreamCreateWithFlags(&pl->s_h2d, cudaStreamNonBlocking));
+    FFTGB_CUDA(cudaStreamCreateWithFlags(&pl->s_d2h, cudaStreamNonBlocking));
+  }
+  const int64_t R = pl->stage_rows;
+  const int64_t nchunk = (pl->batch + R - 1) / R;
+  float2 *slot_in[2] = {pl->d_stage, pl->d_stage + R * pl->N};
+  float2 *slot_out[2] = {pl->d_stage + 2 * R * pl->N, pl->d_stage + 3 * R * pl->N};
+  cudaEvent_t ev_start, ev_in[2], ev_done[2], ev_out[2];
+  FFTGB_CUDA(cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming));
+  for (int i = 0; i < 2; ++i) {
+    FFTGB_CUDA(cudaEventCreateWithFlags(&ev_in[i], cudaEventDisableTiming));
+    FFTGB_CUDA(cudaEventCreateWithFlags(&ev_done[i], cudaEventDisableTiming));
+    FFTGB_CUDA(cudaEventCreateWithFlags(&ev_out[i], cudaEventDisableTiming));
+  }
+  fft_status_t s = FFT_OK;
+  cudaError_t e = cudaEventRecord(ev_start, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(pl->s_h2d, ev_start, 0);
+  const char *hin = (const char *)host_in;
+  char *hout = (char *)host_out;
+  for (int64_t c = 0; c < nchunk && e == cudaSuccess && s == FFT_OK; ++c) {
+    const int slot = (int)(c & 1);
+    const int64_t r0 = c * R, rows = std::min(R, pl->batch - r0);
+    const size_t bytes = (size_t)(rows * row_bytes);
+    if (c >= 2) {  // slot reuse: compute(c-2) read slot_in, D2H(c-2) read slot_out
+      e = cudaStreamWaitEvent(pl->s_h2d, ev_done[slot], 0);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_out[slot], 0);
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(slot_in[slot], hin + r0 * row_bytes, bytes, cudaMemcpyHostToDevice,
+                          pl->s_h2d);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_in[slot], pl->s_h2d);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_in[slot], 0);
+    if (e != cudaSuccess) break;
+    s = exec_rows(pl, slot_in[slot], slot_out[slot], rows, st);
+    if (s != FFT_OK) break;
+    e = cudaEventRecord(ev_done[slot], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(pl->s_d2h, ev_done[slot], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hout + r0 * row_bytes, slot_out[slot], bytes, cudaMemcpyDeviceToHost,
+                          pl->s_d2h);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_out[slot], pl->s_d2h);
+  }
+  if (e == cudaSuccess && s == FFT_OK) e = cudaStreamSynchronize(pl->s_d2h);
+  if (e == cudaSuccess && s == FFT_OK) e = cudaStreamSynchronize(st);
+  cudaEventDestroy(ev_start);
+  for (int i = 0; i < 2; ++i) {
+    cudaEventDestroy(ev_in[i]);
+    cudaEventDestroy(ev_done[i]);
+    cudaEventDestroy(ev_out[i]);
+  }
+  if (s != FFT_OK) return s;
+  return cuda_status(e);
+}
+
+fft_status_t fft_destroy(fft_plan_t plan) {
+  if (!plan) return FFT_OK;
+  free_plan(&plan->impl);
+  delete plan;
+  return FFT_OK;
+}
+
+fft_status_t fft_plan_info(fft_plan_t plan, fft_plan_info_t *info) {
+  if (!plan || !info) return FFT_ERR_INVALID_VALUE;
+  const fft_plan_impl *pl = &plan->impl;
+  memset(info, 0, sizeof(*info));
+  info->N = pl->N;
+  info->batch = pl->batch;
+  info->direction = pl->path == FFT_PATH_RAGGED ? 0 : pl->direction;
+  info->precision = pl->precision;
+  info->path = pl->path;
+  info->scratch_bytes = pl->scratch_bytes;
+  const KernelEntry *k = pl->path == FFT_PATH_SINGLE_CTA ? pl->k_single
+                         : pl->path == FFT_PATH_FOURSTEP ? pl->k_col1
+                                                         : nullptr;
+  if (k) {
+    info->points_per_thread = k->P;
+    info->transforms_per_cta = k->TB;
+    info->threads_per_cta = k->threads;
+    info->num_passes = k->npass;
+    for (int i = 0; i < 8; ++i) info->radix[i] = k->radix[i];
+  }
+  info->n1 = pl->n1;
+  info->n2 = pl->n2;
+  return FFT_OK;
+}
+
+fft_status_t fft_last_device_status(fft_plan_t plan) {
+  if (!plan) return FFT_ERR_INVALID_VALUE;
+  fft_plan_impl *pl = &plan->impl;
+  if (cudaDeviceSynchronize() != cudaSuccess) return FFT_ERR_CUDA;
+  int v = 0;
+  if (cudaMemcpy(&v, pl->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return FFT_ERR_CUDA;
+  if (cudaMemset(pl->d_status, 0, sizeof(int)) != cudaSuccess) return FFT_ERR_CUDA;
+  return (fft_status_t)v;
+}
+
+fft_status_t fft_twiddle_table(fft_plan_t plan, void *host_out, int64_t capacity, int64_t *count) {
+  if (!plan || !count) return FFT_ERR_INVALID_VALUE;
+  const fft_plan_impl *pl = &plan->impl;
+  *count = pl->tw_count;
+  if (host_out && pl->tw_count > 0 && capacity > 0) {
+    const int64_t n = std::min(capacity, pl->tw_count);
+    if (cudaMemcpy(host_out, pl->d_tw, sizeof(float2) * (size_t)n, cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+      return FFT_ERR_CUDA;
+  }
+  return FFT_OK;
+}
+
+fft_status_t fft_twiddle_index(fft_plan_t plan, int64_t pos, int64_t *M, int64_t *e) {
+  if (!plan || !M || !e) return FFT_ERR_INVALID_VALUE;
+  for (const auto &g : plan->impl.tw_segs) {
+    if (pos < g.offset || pos >= g.offset + g.count) continue;
+    const int64_t local = pos - g.offset;
+    if (g.kind == 0) {
+      const int64_t j = local / g.p + 1, k = local % g.p;
+      *M = g.M;
+      *e = j * k;
+    } else {
+      *M = g.M;
+      *e = local;
+    }
+    return FFT_OK;
+  }
+  return FFT_ERR_INVALID_VALUE;
+}
+
+}  // extern "C"

@@ -1,0 +1,173 @@
+// Register-resident DFT butterflies for the Stockham passes.
+//
+// DFT_R on R complex values held in registers, DIT, natural order in and out.
+//   R = 2, 4     written out directly;
+//   R = 8        split-radix DIT (paper Sec. V-B): radix-2 combination of the
+//                even and odd DFT_4, the odd half rotated by W_8^k;
+//   R = 16, 32   the same radix-2 DIT step applied to two DFT_8 / DFT_16.
+// D is the sign of the exponent: D = -1 forward (W = e^{-2 pi i/R}), D = +1
+// inverse.  Multiplications by the constant roots W_R^k use exact special
+// cases for k*8/R integral (1, -i, W_8) and two FMUL + two FFMA otherwise.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace fftgb {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// a * w
+__device__ __forceinline__ float2 cmul(float2 a, float2 w) {
+  return make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
+}
+// a * conj(w)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 w) {
+  return make_float2(fmaf(a.x, w.x, a.y * w.y), fmaf(a.y, w.x, -a.x * w.y));
+}
+// a * w (D = -1) or a * conj(w) (D = +1): tables hold forward roots.
+template <int D>
+__device__ __forceinline__ float2 cmul_dir(float2 a, float2 w) {
+  if constexpr (D < 0) return cmul(a, w);
+  else return cmulc(a, w);
+}
+// a * (D i): multiplication by W_4 (forward: -i, inverse: +i)
+template <int D>
+__device__ __forceinline__ float2 rot90(float2 a) {
+  if constexpr (D < 0) return make_float2(a.y, -a.x);
+  else return make_float2(-a.y, a.x);
+}
+
+// cos(j pi / 16), j = 0..8
+struct Cos16 {
+  static constexpr float c[9] = {1.0f,
+                                 0.98078528040323044913f,
+                                 0.92387953251128675613f,
+                                 0.83146961230254523708f,
+                                 0.70710678118654752440f,
+                                 0.55557023301960222474f,
+                                 0.38268343236508977173f,
+                                 0.19509032201612826785f,
+                                 0.0f};
+};
+
+// v * exp(D * 2 pi i * m / 32) for a compile-time m in [0, 32).
+template <int M, int D>
+__device__ __forceinline__ float2 rot32(float2 v) {
+  constexpr int m = ((M % 32) + 32) % 32;
+  constexpr int q = m / 8, r = m % 8;
+  // cos and sin of the angle 2 pi m / 32 = m pi / 16 (before the sign D)
+  constexpr float c = (q == 0) ? Cos16::c[r] : (q == 1) ? -Cos16::c[8 - r]
+                    : (q == 2) ? -Cos16::c[r] : Cos16::c[8 - r];
+  constexpr float s0 = (q == 0) ? Cos16::c[8 - r] : (q == 1) ? Cos16::c[r]
+                     : (q == 2) ? -Cos16::c[8 - r] : -Cos16::c[r];
+  constexpr float s = (D < 0) ? -s0 : s0;
+  if constexpr (m == 0) {
+    return v;
+  } else if constexpr (m == 8) {
+    return rot90<D>(v);
+  } else if constexpr (m == 16) {
+    return make_float2(-v.x, -v.y);
+  } else if constexpr (m == 24) {
+    return rot90<-D>(v);
+  } else if constexpr (m % 4 == 0) {
+    // odd multiples of pi/4: |c| = |s| = sqrt(1/2)
+    constexpr float h = Cos16::c[4];
+    constexpr float sc = (c > 0.f) ? 1.f : -1.f, ss = (s > 0.f) ? 1.f : -1.f;
+    // (x + i y)(sc + i ss) h = h (sc x - ss y) + i h (ss x + sc y)
+    float re = (sc > 0.f ? v.x : -v.x) - (ss > 0.f ? v.y : -v.y);
+    float im = (ss > 0.f ? v.x : -v.x) + (sc > 0.f ? v.y : -v.y);
+    return make_float2(re * h, im * h);
+  } else {
+    return make_float2(fmaf(v.x, c, -v.y * s), fmaf(v.x, s, v.y * c));
+  }
+}
+
+// v * W_R^{k} with the sign D, for R dividing 32.
+template <int R, int K, int D>
+__device__ __forceinline__ float2 rotR(float2 v) {
+  static_assert(32 % R == 0, "constant roots only for R | 32");
+  return rot32<K * (32 / R), D>(v);
+}
+
+template <int R, int D>
+struct Dft;
+
+template <int D>
+struct Dft<1, D> {
+  static __device__ __forceinline__ void run(float2 (&)[1]) {}
+};
+
+template <int D>
+struct Dft<2, D> {
+  static __device__ __forceinline__ void run(float2 (&a)[2]) {
+    float2 t = a[0];
+    a[0] = cadd(t, a[1]);
+    a[1] = csub(t, a[1]);
+  }
+};
+
+template <int D>
+struct Dft<4, D> {
+  static __device__ __forceinline__ void run(float2 (&a)[4]) {
+    float2 t0 = cadd(a[0], a[2]);
+    float2 t1 = csub(a[0], a[2]);
+    float2 t2 = cadd(a[1], a[3]);
+    float2 t3 = rot90<D>(csub(a[1], a[3]));
+    a[0] = cadd(t0, t2);
+    a[2] = csub(t0, t2);
+    a[1] = cadd(t1, t3);
+    a[3] = csub(t1, t3);
+  }
+};
+
+// Radix-2 DIT step: DFT_R from DFT_{R/2} of the even and odd samples.
+template <int R, int D, int K>
+struct Combine {
+  static __device__ __forceinline__ void run(float2 (&a)[R], const float2 (&e)[R / 2],
+                                             const float2 (&o)[R / 2]) {
+    float2 t = rotR<R, K, D>(o[K]);
+    a[K] = cadd(e[K], t);
+    a[K + R / 2] = csub(e[K], t);
+    if constexpr (K + 1 < R / 2) Combine<R, D, K + 1>::run(a, e, o);
+  }
+};
+
+template <int R, int D>
+struct Dft {
+  static_assert(R == 8 || R == 16 || R == 32, "unsupported radix");
+  static __device__ __forceinline__ void run(float2 (&a)[R]) {
+    float2 e[R / 2], o[R / 2];
+#pragma unroll
+    for (int i = 0; i < R / 2; ++i) {
+      e[i] = a[2 * i];
+      o[i] = a[2 * i + 1];
+    }
+    Dft<R / 2, D>::run(e);
+    Dft<R / 2, D>::run(o);
+    Combine<R, D, 0>::run(a, e, o);
+  }
+};
+
+__host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
+
+// Exchange-buffer layout of one Stockham exchange, chosen by the writing pass
+// (stride p, radix r).  For p >= 16 a warp's writes are runs of 16 consecutive
+// elements and the identity layout is conflict-free.  For p < 16 a half-warp
+// writes at stride p*r; XOR-ing the index bits that carry the lane's high
+// bits (bit log2(p*r) upward) into bits [log2 p, 4) makes the 16 targets of a
+// half-warp land in 16 distinct 8-byte bank pairs, while a 16-aligned run of
+// consecutive indices (the next pass's read) stays a permutation of its block.
+template <int p, int r>
+__device__ __forceinline__ int swz(int idx) {
+  if constexpr (p >= 16) {
+    return idx;
+  } else {
+    constexpr int sh = ilog2(p * r);
+    constexpr int mask = 16 / p - 1;
+    constexpr int tsh = ilog2(p);
+    return idx ^ (((idx >> sh) & mask) << tsh);
+  }
+}
+
+}  // namespace fftgb

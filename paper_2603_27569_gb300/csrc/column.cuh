@@ -1,0 +1,88 @@
+// Column FFTs: batched length-L transforms down the columns of a row-major
+// matrix, C adjacent columns per CTA.  This is the building block of the
+// two-phase four-step path (paper Sec. IV-B, Eq. 2 and Sec. V-D):
+//
+//   N = N1 N2, input index n = n1 + N1 n2, output index k = k2 + N2 k1.
+//   phase 1: for every n1, the N2-point FFT over n2 of x[n1 + N1 n2], times
+//            the four-step twiddle W_N^{n1 k2}, stored as A[n1][k2];
+//   phase 2: for every k2, the N1-point FFT over n1 of A[n1][k2], stored at
+//            X[k2 + N2 k1].
+//
+// Both phases read C consecutive columns of every row, so each warp load
+// covers whole 128-byte segments.  In shared memory element (row, c) of the
+// tile sits at row * C + c: a half-warp always touches 16 consecutive
+// columns, so every exchange is free of bank conflicts without a swizzle.
+// Phase 1 stores its result transposed (column-major) through a padded
+// shared tile so that the global store is coalesced as well.
+#pragma once
+#include "stockham.cuh"
+
+namespace fftgb {
+
+struct ColumnArgs {
+  const float2 *in;
+  float2 *out;
+  const float2 *tw;      // per-pass tables of the length-L transform
+  const float2 *tw_big;  // W_{Ntot}^e, e < Ntot (phase 1 twiddle) or null
+  long long nmat;        // number of matrices (batch)
+  long long in_mat_stride, out_mat_stride;  // elements between matrices
+  int in_row_stride;     // elements between consecutive rows of the input
+  int out_row_stride;    // elements between rows of a non-transposed output
+  int ncols;             // columns per matrix (multiple of C)
+  int ntot;              // L * ncols, the size of the four-step twiddle
+  float scale;
+};
+
+template <int L, int P, int C, int D, class SC, bool TWIDDLE, bool TRANSPOSED>
+__global__ void __launch_bounds__(C *(L / P))
+column_kernel(ColumnArgs args) {
+  static_assert(SC::product() == L, "radix schedule must multiply to L");
+  static_assert(P % SC::max_radix() == 0, "every radix must divide P");
+  constexpr int T = L / P;
+  constexpr int NT = C * T;
+  extern __shared__ float2 smem[];
+  const int c = threadIdx.x % C;
+  const int lt = threadIdx.x / C;
+  const int tiles_per_mat = args.ncols / C;
+  const long long mat = blockIdx.x / tiles_per_mat;
+  const int c0 = (int)(blockIdx.x - mat * tiles_per_mat) * C;
+  float2 a[P];
+  {
+    const float2 *src = args.in + mat * args.in_mat_stride + c0 + c;
+#pragma unroll
+    for (int m = 0; m < P; ++m) a[m] = __ldg(src + (long long)(lt + m * T) * args.in_row_stride);
+  }
+  run_passes<L, P, D, SC, 0>(a, lt, smem, args.tw, Interleaved<C>{c});
+  // a[m] now holds output index final_index(lt, m) of column c0 + c.
+  if constexpr (TWIDDLE) {
+    const int col = c0 + c;
+#pragma unroll
+    for (int m = 0; m < P; ++m) {
+      const int k = final_index<L, P, SC>(lt, m);
+      const int e = (col * k) & (args.ntot - 1);
+      a[m] = cmul_dir<D>(a[m], __ldg(args.tw_big + e));
+    }
+  }
+  if constexpr (TRANSPOSED) {
+    // out[col * L + k]: stage through a tile padded to C + 1 columns.
+    constexpr int LD = C + 1;
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < P; ++m) smem[final_index<L, P, SC>(lt, m) * LD + c] = a[m];
+    __syncthreads();
+    float2 *dst = args.out + mat * args.out_mat_stride + (long long)c0 * L;
+#pragma unroll
+    for (int u = 0; u < P; ++u) {
+      const int e = threadIdx.x + u * NT;  // e = col_local * L + k
+      const int cl = e / L, k = e - cl * L;
+      dst[e] = cscale(smem[k * LD + cl], args.scale);
+    }
+  } else {
+    float2 *dst = args.out + mat * args.out_mat_stride + c0 + c;
+#pragma unroll
+    for (int m = 0; m < P; ++m)
+      dst[(long long)final_index<L, P, SC>(lt, m) * args.out_row_stride] = cscale(a[m], args.scale);
+  }
+}
+
+}  // namespace fftgb

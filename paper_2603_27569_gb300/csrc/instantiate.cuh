@@ -1,0 +1,61 @@
+// Helpers that instantiate a kernel configuration and register it.
+#pragma once
+#include "column.cuh"
+#include "registry.h"
+#include "stockham.cuh"
+
+namespace fftgb {
+
+template <class SC>
+inline void fill_radix(KernelEntry &e) {
+  e.npass = SC::npass;
+  for (int i = 0; i < 8; ++i) e.radix[i] = i < SC::npass ? SC::radix[i] : 0;
+  e.tw_total = SC::tw_total();
+}
+
+template <int N, int P, int TB, int DEF, class SC>
+inline KernelEntry stockham_entry() {
+  KernelEntry e{};
+  e.kind = KIND_STOCKHAM;
+  e.N = N;
+  e.P = P;
+  e.TB = TB;
+  e.threads = TB * (N / P);
+  e.smem = sizeof(float2) * (size_t)TB * N;
+  fill_radix<SC>(e);
+  e.is_default = DEF;
+  e.variant = 0;
+  e.fn[0] = (const void *)&stockham_kernel<N, P, TB, -1, SC>;
+  e.fn[1] = (const void *)&stockham_kernel<N, P, TB, +1, SC>;
+  return e;
+}
+
+template <int L, int P, int C, int VAR, int DEF, class SC>
+inline KernelEntry column_entry() {
+  KernelEntry e{};
+  e.kind = KIND_COLUMN;
+  e.N = L;
+  e.P = P;
+  e.TB = C;
+  e.threads = C * (L / P);
+  e.smem = sizeof(float2) * (size_t)L * (VAR ? C + 1 : C);
+  fill_radix<SC>(e);
+  e.is_default = DEF;
+  e.variant = VAR;
+  e.fn[0] = (const void *)&column_kernel<L, P, C, -1, SC, VAR != 0, VAR != 0>;
+  e.fn[1] = (const void *)&column_kernel<L, P, C, +1, SC, VAR != 0, VAR != 0>;
+  return e;
+}
+
+}  // namespace fftgb
+
+#define FFTGB_CAT2(a, b) a##b
+#define FFTGB_CAT(a, b) FFTGB_CAT2(a, b)
+// FFTGB_STOCKHAM(N, P, TB, is_default, radices...)
+#define FFTGB_STOCKHAM(N, P, TB, DEF, ...)                                   \
+  static ::fftgb::Registrar FFTGB_CAT(fftgb_reg_, __COUNTER__)(              \
+      ::fftgb::stockham_entry<N, P, TB, DEF, ::fftgb::Sched<__VA_ARGS__>>())
+// FFTGB_COLUMN(L, P, C, variant, is_default, radices...)
+#define FFTGB_COLUMN(L, P, C, VAR, DEF, ...)                                 \
+  static ::fftgb::Registrar FFTGB_CAT(fftgb_reg_, __COUNTER__)(              \
+      ::fftgb::column_entry<L, P, C, VAR, DEF, ::fftgb::Sched<__VA_ARGS__>>())

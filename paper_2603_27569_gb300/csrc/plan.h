@@ -1,0 +1,96 @@
+// Internal plan representation shared by the C-ABI translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fftgb.h"
+#include "registry.h"
+
+namespace fftgb {
+
+// One segment of a plan's twiddle allocation.
+struct TwSeg {
+  int64_t offset;  // first entry
+  int64_t count;   // entries
+  int kind;        // 0: per-pass table W_{p r}^{j k} laid out [j-1][k]; 1: W_M^e, e < M
+  int p, r;        // kind 0
+  int64_t M;       // kind 1 (and p*r for kind 0)
+};
+
+struct RaggedState;  // ragged.cu
+
+struct fft_plan_impl {
+  int N = 0;
+  int64_t batch = 0;
+  int direction = -1;
+  int precision = FFT_PREC_FP32;
+  int flags = 0;
+  int path = 0;
+  float scale = 1.f;
+  int device = 0;
+  // single-CTA path
+  const KernelEntry *k_single = nullptr;
+  // four-step path: phase-1 and phase-2 column kernels, split N = n1 * n2
+  const KernelEntry *k_col1 = nullptr, *k_col2 = nullptr;
+  int n1 = 0, n2 = 0;
+  // twiddles
+  float2 *d_tw = nullptr;
+  int64_t tw_count = 0;
+  std::vector<TwSeg> tw_segs;
+  int64_t tw_single = 0, tw_col1 = 0, tw_col2 = 0, tw_big = 0;  // offsets
+  // scratch (four-step intermediate)
+  float2 *d_scratch = nullptr;
+  int64_t scratch_bytes = 0;
+  // device status word (bounded waits report here)
+  int *d_status = nullptr;
+  // host-buffer exec staging
+  float2 *d_stage = nullptr;
+  int64_t stage_rows = 0;
+  cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+  // tensor-core path
+  void *tc = nullptr;
+  // ragged path
+  RaggedState *ragged = nullptr;
+};
+
+// Helpers implemented in api.cu, shared with the other units.
+fft_status_t cuda_status(cudaError_t e);
+fft_status_t build_twiddles(fft_plan_impl *pl, const std::vector<TwSeg> &segs);
+std::vector<TwSeg> pass_segments(const KernelEntry &k, int64_t &offset);
+const KernelEntry *find_stockham(int N, int P, int TB, const int *radix, int npass);
+const KernelEntry *default_stockham(int N);
+const KernelEntry *default_column(int L, int variant);
+fft_status_t launch_stockham(const KernelEntry *k, int dir, const float2 *in, float2 *out,
+                             const float2 *tw, int64_t rows, float scale, cudaStream_t st);
+fft_status_t exec_rows(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t rows,
+                       cudaStream_t st);
+fft_status_t ensure_smem_attr(const KernelEntry *k);
+
+// Autotuner cache lookup (autotune.cu).  Returns true and fills the choice if
+// the process-wide cache holds one for this key.
+struct TuneChoice {
+  int path;                 // FFT_PATH_SINGLE_CTA or FFT_PATH_FOURSTEP
+  int P, TB, npass;
+  int radix[8];
+  int n1;                   // four-step split (n1)
+};
+bool tune_lookup(int N, int direction, int precision, TuneChoice *out);
+
+// Tensor-core path (tc.cu)
+fft_status_t tc_plan(fft_plan_impl *pl);
+fft_status_t tc_exec(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t rows,
+                     cudaStream_t st);
+void tc_destroy(fft_plan_impl *pl);
+
+// Ragged path (ragged.cu)
+fft_status_t ragged_exec(fft_plan_impl *pl, const float2 *in, float2 *out, cudaStream_t st);
+void ragged_destroy(fft_plan_impl *pl);
+
+}  // namespace fftgb
+
+struct fft_plan_s {
+  fftgb::fft_plan_impl impl;
+};

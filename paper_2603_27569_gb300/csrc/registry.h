@@ -1,0 +1,35 @@
+// Kernel registry: every compiled kernel configuration registers itself here
+// at library load, so the planner and the autotuner can enumerate them.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include <vector>
+
+namespace fftgb {
+
+enum KernelKind { KIND_STOCKHAM = 1, KIND_COLUMN = 2 };
+
+struct KernelEntry {
+  int kind;
+  int N;          // transform length (L for column kernels)
+  int P;          // complex points per thread
+  int TB;         // rows per CTA (single-CTA) / columns per CTA (column)
+  int threads;    // threads per CTA
+  size_t smem;    // dynamic shared memory bytes
+  int npass;
+  int radix[8];
+  int tw_total;   // entries of the per-pass twiddle tables
+  int is_default; // the built-in choice for this (kind, N, variant)
+  int variant;    // column kernels: 0 plain, 1 twiddle + transposed store
+  const void *fn[2];  // [0] forward (D = -1), [1] inverse (D = +1)
+};
+
+void register_kernel(const KernelEntry &e);
+const std::vector<KernelEntry> &kernel_registry();
+
+struct Registrar {
+  explicit Registrar(const KernelEntry &e) { register_kernel(e); }
+};
+
+}  // namespace fftgb

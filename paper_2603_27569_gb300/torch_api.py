@@ -1,0 +1,229 @@
+"""PyTorch-facing wrappers over the C ABI: plans, ``fft``/``ifft`` and autograd.
+
+PyTorch provides device memory and the current stream; every transform,
+pointwise multiply and reduction runs in libfftgb's kernels.
+
+Differentiation (the adjoint of a linear map is its conjugate transpose):
+  y = F x     (unnormalised forward)   ->  grad_x = F^H grad_y
+  y = G x     (inverse, G = F^H / N)   ->  grad_x = G^H grad_y = (1/N) F grad_y
+Both adjoints are library plans built with FFT_FLAG_ADJOINT.  Complex
+gradients follow PyTorch's convention grad = dL/dRe + i dL/dIm.
+
+SpectralFilter implements SAR range compression (paper Sec. II-D):
+  y = IFFT(FFT(x) * H), with H learnable.
+  backward: g_z = G^H g_y;  grad_H = sum_rows conj(FFT(x)) * g_z;
+            grad_x = F^H (conj(H) * g_z).
+"""
+from __future__ import annotations
+
+import collections
+import threading
+
+import torch
+
+from . import _binding as B
+
+__all__ = ["Plan", "get_plan", "fft", "ifft", "fft_host", "SpectralFilter",
+           "spectral_filter", "clear_plan_cache"]
+
+_PREC = {"fp32": B.FFT_PREC_FP32, "fp16x2": B.FFT_PREC_FP16X2, "bf16x2": B.FFT_PREC_BF16X2}
+
+
+def _check_tensor(x: torch.Tensor, N: int, batch: int, what: str) -> None:
+    if not isinstance(x, torch.Tensor):
+        raise TypeError(f"{what} must be a torch.Tensor")
+    if x.dtype != torch.complex64:
+        raise TypeError(f"{what} must be complex64, got {x.dtype}")
+    if not x.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if x.numel() != N * batch:
+        raise ValueError(f"{what} has {x.numel()} elements, plan needs {N * batch}")
+
+
+class Plan:
+    """Owns one fft_plan_t on one CUDA device."""
+
+    def __init__(self, N: int, batch: int, direction: int = B.FFT_FORWARD, precision: int = 0,
+                 flags: int = 0, config: dict | None = None, device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
+            else torch.device(device)
+        with torch.cuda.device(self.device):
+            if config is not None:
+                self.handle = B.fft_plan_config(N, batch, direction, config, flags)
+            else:
+                self.handle = B.fft_plan_ex(N, batch, direction, precision, flags)
+        self.N, self.batch, self.direction = N, batch, direction
+        self.precision, self.flags = precision, flags
+
+    def __call__(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        return self.exec(x, out, stream)
+
+    def exec(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        if not x.is_cuda or x.device != self.device:
+            raise ValueError(f"input must live on {self.device}")
+        _check_tensor(x, self.N, self.batch, "input")
+        if out is None:
+            out = torch.empty_like(x)
+        else:
+            _check_tensor(out, self.N, self.batch, "output")
+        st = torch.cuda.current_stream(self.device) if stream is None else stream
+        B.fft_exec(self.handle, x, out, st)
+        return out
+
+    def exec_host(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        """Transform a host (ideally pinned) complex64 tensor; returns a host tensor."""
+        if x.is_cuda:
+            raise ValueError("exec_host takes a host tensor")
+        _check_tensor(x, self.N, self.batch, "input")
+        if out is None:
+            out = torch.empty_like(x, pin_memory=x.is_pinned())
+        else:
+            _check_tensor(out, self.N, self.batch, "output")
+        with torch.cuda.device(self.device):
+            st = torch.cuda.current_stream(self.device) if stream is None else stream
+            B.fft_exec_host(self.handle, x, out, st)
+        return out
+
+    def info(self) -> dict:
+        return B.fft_plan_info(self.handle)
+
+    def device_status(self) -> int:
+        return B.fft_last_device_status(self.handle)
+
+    def close(self) -> None:
+        h, self.handle = getattr(self, "handle", None), None
+        if h:
+            try:
+                with torch.cuda.device(self.device):
+                    B.fft_destroy(h)
+            except Exception:
+                pass
+
+    def __del__(self):
+        self.close()
+
+
+_cache: "collections.OrderedDict[tuple, Plan]" = collections.OrderedDict()
+_cache_lock = threading.Lock()
+_CACHE_MAX = 64
+
+
+def get_plan(N: int, batch: int, direction: int, precision: int = 0, flags: int = 0,
+             device=None) -> Plan:
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None \
+        else torch.device(device)
+    key = (dev.index, N, batch, direction, precision, flags)
+    with _cache_lock:
+        p = _cache.get(key)
+        if p is not None:
+            _cache.move_to_end(key)
+            return p
+    p = Plan(N, batch, direction, precision, flags, device=dev)
+    with _cache_lock:
+        _cache[key] = p
+        while len(_cache) > _CACHE_MAX:
+            _cache.popitem(last=False)
+    return p
+
+
+def clear_plan_cache() -> None:
+    with _cache_lock:
+        _cache.clear()
+
+
+def _raw(x: torch.Tensor, direction: int, precision: int, flags: int, out=None) -> torch.Tensor:
+    N = x.shape[-1]
+    batch = x.numel() // N if N else 0
+    plan = get_plan(N, batch, direction, precision, flags, x.device)
+    return plan.exec(x.contiguous(), out).view(x.shape)
+
+
+class _FFTFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x, direction, precision, flags):
+        ctx.direction, ctx.precision, ctx.flags = direction, precision, flags
+        return _raw(x, direction, precision, flags)
+
+    @staticmethod
+    def backward(ctx, g):
+        gx = _raw(g.contiguous(), ctx.direction, ctx.precision, ctx.flags | B.FFT_FLAG_ADJOINT)
+        return gx, None, None, None
+
+
+def fft(x: torch.Tensor, inverse: bool = False, precision: str = "fp32",
+        unnormalized_inverse: bool = False) -> torch.Tensor:
+    """Batched C2C FFT along the last dimension of a CUDA complex64 tensor.
+
+    forward: unnormalised, W_N = exp(-2 pi i / N); inverse: scaled by 1/N
+    unless ``unnormalized_inverse``.  Differentiable (adjoint plans).
+    """
+    direction = B.FFT_INVERSE if inverse else B.FFT_FORWARD
+    flags = B.FFT_FLAG_UNNORMALIZED_INVERSE if unnormalized_inverse else 0
+    prec = _PREC[precision]
+    if torch.is_grad_enabled() and x.requires_grad:
+        return _FFTFn.apply(x, direction, prec, flags)
+    return _raw(x, direction, prec, flags)
+
+
+def ifft(x: torch.Tensor, precision: str = "fp32") -> torch.Tensor:
+    return fft(x, inverse=True, precision=precision)
+
+
+def fft_host(x: torch.Tensor, inverse: bool = False, device=None) -> torch.Tensor:
+    """Host tensor in, host tensor out; copies pipelined with the transforms."""
+    N = x.shape[-1]
+    batch = x.numel() // N
+    plan = get_plan(N, batch, B.FFT_INVERSE if inverse else B.FFT_FORWARD, 0, 0, device)
+    return plan.exec_host(x.contiguous()).view(x.shape)
+
+
+class _SpectralFilterFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x, H):
+        N = x.shape[-1]
+        batch = x.numel() // N
+        xc = x.contiguous()
+        Hc = H.contiguous()
+        X = _raw(xc, B.FFT_FORWARD, 0, 0)                       # F x
+        Z = torch.empty_like(X)
+        st = torch.cuda.current_stream(x.device)
+        B.fft_filter_apply(X, Hc, Z, N, batch, False, 1.0, st)   # F x * H
+        y = _raw(Z, B.FFT_INVERSE, 0, 0, out=Z)                   # G (F x * H), in place
+        ctx.save_for_backward(X, Hc)
+        ctx.shape = x.shape
+        return y.view(x.shape)
+
+    @staticmethod
+    def backward(ctx, gy):
+        X, H = ctx.saved_tensors
+        N = X.shape[-1]
+        batch = X.numel() // N
+        st = torch.cuda.current_stream(X.device)
+        gz = _raw(gy.contiguous(), B.FFT_INVERSE, 0, B.FFT_FLAG_ADJOINT)  # G^H g_y = F g_y / N
+        grad_x = grad_H = None
+        if ctx.needs_input_grad[1]:
+            grad_H = torch.empty(N, dtype=torch.complex64, device=X.device)
+            ws = B.fft_filter_grad_h_workspace(N, batch)
+            work = torch.empty(max(ws, 8), dtype=torch.uint8, device=X.device)
+            B.fft_filter_grad_h(X, gz, grad_H, N, batch, work, st)
+        if ctx.needs_input_grad[0]:
+            B.fft_filter_apply(gz, H, gz, N, batch, True, 1.0, st)           # conj(H) g_z
+            grad_x = _raw(gz, B.FFT_FORWARD, 0, B.FFT_FLAG_ADJOINT, out=gz)  # F^H (.)
+            grad_x = grad_x.view(ctx.shape)
+        return grad_x, grad_H
+
+
+def spectral_filter(x: torch.Tensor, H: torch.Tensor) -> torch.Tensor:
+    """y = IFFT(FFT(x) * H) along the last dimension; differentiable in x and H."""
+    return _SpectralFilterFn.apply(x, H)
+
+
+class SpectralFilter(torch.nn.Module):
+    """Learnable matched filter H (complex64 [N]) applied in the frequency domain."""
+
+    def __init__(self, H: torch.Tensor):
+        super().__init__()
+        self.H = torch.nn.Parameter(H.detach().clone().to(torch.complex64))
+
+    def forward(self, x: torch.Tensor) -> torch.Tensor:
+        return spectral_filter(x, self.H)

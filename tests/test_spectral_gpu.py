@@ -1,0 +1,80 @@
+"""Differentiable spectral filter (SAR range compression) and FFT autograd on
+the GPU path, against the oracle's analytic gradient (itself pinned to FP64
+central differences in test_oracle.py)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2603_27569_gb300 as fg
+from paper_2603_27569_gb300 import synth
+from gpu_util import NTHREADS, TOL_FP32, TOL_GRAD, rel_l2_rows, to_dev, to_host
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2603_27569_gb300 import build
+
+    build.build()
+
+
+def rel(a, b):
+    a = np.asarray(a, np.complex128)
+    b = np.asarray(b, np.complex128)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def sar_case(rows, N, Np, seed=0):
+    x, pulse = synth.sar_echoes(rows, N, Np=Np, seed=seed)
+    H = np.conj(oracle.fft(pulse)).astype(np.complex64)
+    m = synth.real_mask((rows, N), seed=2)
+    return x, H, m
+
+
+def gpu_filter_grads(x, H, m):
+    xd = to_dev(x).requires_grad_(True)
+    layer = fg.SpectralFilter(to_dev(H))
+    y = layer(xd)
+    md = to_dev(m)
+    loss = (md * (y.real ** 2 + y.imag ** 2)).sum()
+    loss.backward()
+    torch.cuda.synchronize()
+    return to_host(y), to_host(xd.grad), to_host(layer.H.grad), float(loss)
+
+
+@pytest.mark.parametrize("rows,N,Np", [(4, 256, 64), (64, 8192, 2048), (3, 16384, 4096)])
+def test_spectral_filter_forward_and_grads_match_oracle(rows, N, Np):
+    x, H, m = sar_case(rows, N, Np)
+    y, gx, gH, loss = gpu_filter_grads(x, H, m)
+    want_y = oracle.spectral_filter_forward(x, H)
+    assert rel_l2_rows(y, want_y).max() <= 2 * TOL_FP32
+    ogx, ogH = oracle.spectral_filter_grads(x, H, m)
+    assert rel(gx, ogx) <= TOL_GRAD
+    assert rel(gH, ogH) <= TOL_GRAD
+    assert abs(loss - oracle.spectral_filter_loss(x, H, m)) <= 1e-5 * abs(loss)
+
+
+def test_spectral_filter_grad_h_is_bitwise_reproducible():
+    x, H, m = sar_case(100, 1024, 256, seed=4)
+    _, _, g1, _ = gpu_filter_grads(x, H, m)
+    _, _, g2, _ = gpu_filter_grads(x, H, m)
+    assert np.array_equal(g1.view(np.uint32), g2.view(np.uint32))
+
+
+@pytest.mark.parametrize("N", [256, 16384])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_fft_autograd_uses_the_adjoint(N, inverse):
+    # L = sum m |T x|^2  ->  grad_x = T^H (2 m T x), T = F or G
+    x = synth.gaussian((3, N), seed=5)
+    m = synth.real_mask((3, N), seed=6)
+    xd = to_dev(x).requires_grad_(True)
+    y = fg.fft(xd, inverse=inverse)
+    loss = (to_dev(m) * (y.real ** 2 + y.imag ** 2)).sum()
+    loss.backward()
+    g = to_host(xd.grad)
+    Tx = oracle.fft(x, inverse=inverse)
+    gy = 2.0 * m * Tx
+    want = N * oracle.ifft(gy) if not inverse else oracle.fft(gy) / N
+    assert rel(g, want) <= TOL_GRAD
