@@ -92,6 +92,9 @@ typedef struct {
     int radix[8];           /* radix of each pass, first pass first           */
     int n1, n2;             /* four-step split N = n1 * n2 (0 otherwise)       */
     int64_t scratch_bytes;  /* device scratch owned by the plan               */
+    int twiddle_mode;       /* as in fft_config_t                              */
+    int grid_ctas;          /* CTAs launched per exec (0 = one per tile)      */
+    int tma_slabs;          /* as in fft_config_t                              */
 } fft_plan_info_t;
 
 /* One compiled execution configuration (see fft_list_configs). */
@@ -103,6 +106,14 @@ typedef struct {
     int num_passes;
     int radix[8];           /* radix schedule of the (first) kernel              */
     int n1;                 /* four-step: N = n1 * (N / n1); 0 otherwise         */
+    int twiddle_mode;       /* 0: every twiddle read from its table; 1: W^k and
+                               W^{4k} (W^{16k}) read, the rest formed as products */
+    int ctas_per_sm;        /* 0: one CTA per tile; -1: persistent grid at full
+                               occupancy with L2 prefetch of the next tile;
+                               k > 0: persistent with k CTAs per SM             */
+    int tma_slabs;          /* > 0: TMA-staged persistent kernel keeping this many
+                               slabs of the next row in a shared-memory ring;
+                               0: pass 0 loads straight from global memory      */
 } fft_config_t;
 
 /* Human-readable name of a status code (static string, never NULL). */

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "column.cuh"
+#include "staged.cuh"
 #include "plan.h"
 
 namespace fftgb {
@@ -37,9 +38,23 @@ static std::vector<KernelEntry> &registry_storage() {
 void register_kernel(const KernelEntry &e) { registry_storage().push_back(e); }
 const std::vector<KernelEntry> &kernel_registry() { return registry_storage(); }
 
-const KernelEntry *find_stockham(int N, int P, int TB, const int *radix, int npass) {
+const KernelEntry *find_stockham(int N, int P, int TB, const int *radix, int npass, int twm) {
   for (const auto &e : kernel_registry()) {
-    if (e.kind != KIND_STOCKHAM || e.N != N || e.P != P || e.TB != TB || e.npass != npass) continue;
+    if (e.kind != KIND_STOCKHAM || e.N != N || e.P != P || e.TB != TB || e.npass != npass ||
+        e.twm != twm)
+      continue;
+    bool same = true;
+    for (int i = 0; i < npass; ++i) same = same && e.radix[i] == radix[i];
+    if (same) return &e;
+  }
+  return nullptr;
+}
+
+const KernelEntry *find_staged(int N, int P, int C, const int *radix, int npass, int twm) {
+  for (const auto &e : kernel_registry()) {
+    if (e.kind != KIND_STAGED || e.N != N || e.P != P || e.slabs != C || e.npass != npass ||
+        e.twm != twm)
+      continue;
     bool same = true;
     for (int i = 0; i < npass; ++i) same = same && e.radix[i] == radix[i];
     if (same) return &e;
@@ -50,9 +65,9 @@ const KernelEntry *find_stockham(int N, int P, int TB, const int *radix, int npa
 const KernelEntry *default_stockham(int N) {
   const KernelEntry *any = nullptr;
   for (const auto &e : kernel_registry()) {
-    if (e.kind != KIND_STOCKHAM || e.N != N) continue;
+    if ((e.kind != KIND_STOCKHAM && e.kind != KIND_STAGED) || e.N != N) continue;
     if (e.is_default) return &e;
-    if (!any) any = &e;
+    if (!any && e.kind == KIND_STOCKHAM) any = &e;
   }
   return any;
 }
@@ -150,8 +165,23 @@ fft_status_t build_twiddles(fft_plan_impl *pl, const std::vector<TwSeg> &segs) {
 // ---------------------------------------------------------------------------
 // Launch helpers
 // ---------------------------------------------------------------------------
+int64_t persistent_grid(const KernelEntry *k, int per_sm) {
+  int dev = 0, sms = 0, occ = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k->fn[0], k->threads, k->smem) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (occ < 1) occ = 1;
+  const int use = (per_sm < 0 || per_sm > occ) ? occ : per_sm;
+  return (int64_t)use * sms;
+}
+
 fft_status_t launch_stockham(const KernelEntry *k, int dir, const float2 *in, float2 *out,
-                             const float2 *tw, int64_t rows, float scale, cudaStream_t st) {
+                             const float2 *tw, int64_t rows, float scale, int64_t grid_cap,
+                             cudaStream_t st) {
   if (rows <= 0) return FFT_OK;
   StockhamArgs a;
   a.in = in;
@@ -159,8 +189,27 @@ fft_status_t launch_stockham(const KernelEntry *k, int dir, const float2 *in, fl
   a.tw = tw;
   a.batch = rows;
   a.scale = scale;
-  const int64_t grid = (rows + k->TB - 1) / k->TB;
+  int64_t grid = (rows + k->TB - 1) / k->TB;
+  if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;
   if (grid > 0x7fffffffLL) return FFT_ERR_INVALID_SIZE;
+  void *args[] = {&a};
+  FFTGB_CUDA(cudaLaunchKernel(k->fn[dir > 0 ? 1 : 0], dim3((unsigned)grid), dim3(k->threads),
+                              args, k->smem, st));
+  return FFT_OK;
+}
+
+static fft_status_t launch_staged(const KernelEntry *k, int dir, const float2 *in, float2 *out,
+                                  const float2 *tw, int64_t rows, float scale, int64_t grid,
+                                  int *status, cudaStream_t st) {
+  if (rows <= 0) return FFT_OK;
+  StagedArgs a;
+  a.in = in;
+  a.out = out;
+  a.tw = tw;
+  a.batch = rows;
+  a.scale = scale;
+  a.status = status;
+  if (grid <= 0 || grid > rows) grid = rows;
   void *args[] = {&a};
   FFTGB_CUDA(cudaLaunchKernel(k->fn[dir > 0 ? 1 : 0], dim3((unsigned)grid), dim3(k->threads),
                               args, k->smem, st));
@@ -182,9 +231,13 @@ static fft_status_t launch_column(const KernelEntry *k, int dir, const ColumnArg
 fft_status_t exec_rows(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t rows,
                        cudaStream_t st) {
   if (rows <= 0) return FFT_OK;
+  if (pl->path == FFT_PATH_SINGLE_CTA && pl->k_single->kind == KIND_STAGED) {
+    return launch_staged(pl->k_single, pl->direction, in, out, pl->d_tw + pl->tw_single, rows,
+                         pl->scale, pl->grid_ctas, pl->d_status, st);
+  }
   if (pl->path == FFT_PATH_SINGLE_CTA) {
     return launch_stockham(pl->k_single, pl->direction, in, out, pl->d_tw + pl->tw_single, rows,
-                           pl->scale, st);
+                           pl->scale, pl->grid_ctas, st);
   }
   if (pl->path == FFT_PATH_FOURSTEP) {
     ColumnArgs c1{};
@@ -222,6 +275,9 @@ fft_status_t exec_rows(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t
 }
 
 static bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Built-in launch shape of the single-CTA path: persistent at full occupancy.
+constexpr int kDefaultCtasPerSm = -1;
 
 // Four-step split N = n1 * n2 with both factors column-kernel lengths (16..256).
 static bool fourstep_split(int N, int want_n1, int *n1, int *n2) {
@@ -285,12 +341,15 @@ static fft_status_t plan_fourstep(fft_plan_impl *pl, int want_n1) {
   return FFT_OK;
 }
 
-static fft_status_t plan_single(fft_plan_impl *pl, const KernelEntry *k) {
+static fft_status_t plan_single(fft_plan_impl *pl, const KernelEntry *k, int ctas_per_sm) {
   if (!k) return FFT_ERR_NOT_SUPPORTED;
   pl->path = FFT_PATH_SINGLE_CTA;
   pl->k_single = k;
   fft_status_t s = ensure_smem_attr(k);
   if (s != FFT_OK) return s;
+  if (k->kind == KIND_STAGED) ctas_per_sm = 1;  // one resident CTA per SM by design
+  pl->ctas_per_sm = ctas_per_sm;
+  pl->grid_ctas = ctas_per_sm != 0 ? persistent_grid(k, ctas_per_sm) : 0;
   int64_t off = 0;
   pl->tw_single = 0;
   auto segs = pass_segments(*k, off);
@@ -373,9 +432,13 @@ static fft_status_t plan_common(fft_plan_t *out, int N, int64_t batch, int direc
       if (cfg->path == FFT_PATH_FOURSTEP) {
         s = plan_fourstep(pl, cfg->n1);
       } else if (cfg->path == FFT_PATH_SINGLE_CTA) {
-        const KernelEntry *k = find_stockham(N, cfg->points_per_thread, cfg->transforms_per_cta,
-                                             cfg->radix, cfg->num_passes);
-        s = k ? plan_single(pl, k) : FFT_ERR_NOT_SUPPORTED;
+        const KernelEntry *k =
+            cfg->tma_slabs > 0
+                ? find_staged(N, cfg->points_per_thread, cfg->tma_slabs, cfg->radix,
+                              cfg->num_passes, cfg->twiddle_mode)
+                : find_stockham(N, cfg->points_per_thread, cfg->transforms_per_cta, cfg->radix,
+                                cfg->num_passes, cfg->twiddle_mode);
+        s = k ? plan_single(pl, k, cfg->ctas_per_sm) : FFT_ERR_NOT_SUPPORTED;
       } else {
         s = FFT_ERR_INVALID_VALUE;
       }
@@ -384,7 +447,7 @@ static fft_status_t plan_common(fft_plan_t *out, int N, int64_t batch, int direc
     } else if (flags & FFT_FLAG_FORCE_FOURSTEP) {
       s = plan_fourstep(pl, 0);
     } else if (flags & FFT_FLAG_FORCE_SINGLE_CTA) {
-      s = plan_single(pl, default_stockham(N));
+      s = plan_single(pl, default_stockham(N), kDefaultCtasPerSm);
     } else {
       TuneChoice tc;
       bool have = !(flags & FFT_FLAG_NO_AUTOTUNE_CACHE) &&
@@ -393,11 +456,13 @@ static fft_status_t plan_common(fft_plan_t *out, int N, int64_t batch, int direc
         s = plan_fourstep(pl, tc.n1);
         if (s == FFT_ERR_NOT_SUPPORTED) have = false;
       } else if (have) {
-        const KernelEntry *k = find_stockham(N, tc.P, tc.TB, tc.radix, tc.npass);
-        if (k) s = plan_single(pl, k);
+        const KernelEntry *k = tc.slabs > 0
+                                   ? find_staged(N, tc.P, tc.slabs, tc.radix, tc.npass, tc.twm)
+                                   : find_stockham(N, tc.P, tc.TB, tc.radix, tc.npass, tc.twm);
+        if (k) s = plan_single(pl, k, tc.ctas_per_sm);
         else have = false;
       }
-      if (!have) s = plan_single(pl, default_stockham(N));
+      if (!have) s = plan_single(pl, default_stockham(N), kDefaultCtasPerSm);
     }
   }
   if (s != FFT_OK) {
@@ -435,14 +500,33 @@ int fft_list_configs(int N, fft_config_t *out, int capacity) {
   if (!is_pow2(N) || N < 2 || N > 16384) return 0;
   for (const auto &e : kernel_registry()) {
     if (e.kind != KIND_STOCKHAM || e.N != N) continue;
+    for (int shape : {0, -1}) {
+      fft_config_t c;
+      memset(&c, 0, sizeof(c));
+      c.path = FFT_PATH_SINGLE_CTA;
+      c.points_per_thread = e.P;
+      c.transforms_per_cta = e.TB;
+      c.threads_per_cta = e.threads;
+      c.num_passes = e.npass;
+      for (int i = 0; i < 8; ++i) c.radix[i] = e.radix[i];
+      c.twiddle_mode = e.twm;
+      c.ctas_per_sm = shape;
+      emit(c);
+    }
+  }
+  for (const auto &e : kernel_registry()) {
+    if (e.kind != KIND_STAGED || e.N != N) continue;
     fft_config_t c;
     memset(&c, 0, sizeof(c));
     c.path = FFT_PATH_SINGLE_CTA;
     c.points_per_thread = e.P;
-    c.transforms_per_cta = e.TB;
+    c.transforms_per_cta = 1;
     c.threads_per_cta = e.threads;
     c.num_passes = e.npass;
     for (int i = 0; i < 8; ++i) c.radix[i] = e.radix[i];
+    c.twiddle_mode = e.twm;
+    c.ctas_per_sm = 1;
+    c.tma_slabs = e.slabs;
     emit(c);
   }
   for (int a = 16; a <= 256; a *= 2) {
@@ -587,6 +671,9 @@ fft_status_t fft_plan_info(fft_plan_t plan, fft_plan_info_t *info) {
   }
   info->n1 = pl->n1;
   info->n2 = pl->n2;
+  info->twiddle_mode = pl->path == FFT_PATH_SINGLE_CTA ? pl->k_single->twm : 0;
+  info->grid_ctas = (int)pl->grid_ctas;
+  info->tma_slabs = pl->path == FFT_PATH_SINGLE_CTA ? pl->k_single->slabs : 0;
   return FFT_OK;
 }
 

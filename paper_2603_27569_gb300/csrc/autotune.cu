@@ -1,0 +1,245 @@
+// Autotuner: times every compiled configuration for (N, direction) on the
+// current GPU and remembers the fastest in a process-wide cache that later
+// plans consult.  Candidates are the single-CTA Stockham variants (points per
+// thread = radix schedule, transforms per CTA) and every four-step split.
+// The cache can be written to / read from a JSON file keyed by GPU name.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "plan.h"
+
+namespace fftgb {
+
+namespace {
+
+struct Key {
+  int N, dir, prec;
+  bool operator<(const Key &o) const {
+    return std::tie(N, dir, prec) < std::tie(o.N, o.dir, o.prec);
+  }
+};
+
+struct Entry {
+  TuneChoice choice;
+  double us;  // measured time of one exec of the tuning batch
+  int64_t batch;
+};
+
+std::mutex g_mu;
+std::map<Key, Entry> g_cache;
+bool g_env_loaded = false;
+
+std::string gpu_name() {
+  int dev = 0;
+  cudaDeviceProp p;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&p, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return "unknown";
+  }
+  return std::string(p.name);
+}
+
+__global__ void fill_pattern(float2 *x, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    // a cheap deterministic non-trivial pattern (values in [-1, 1))
+    uint32_t h = (uint32_t)(i * 2654435761u);
+    x[i] = make_float2((float)(h & 0xffff) / 32768.f - 1.f, (float)(h >> 16) / 32768.f - 1.f);
+  }
+}
+
+fft_status_t write_json(const char *path) {
+  FILE *f = fopen(path, "w");
+  if (!f) return FFT_ERR_INVALID_VALUE;
+  std::string gpu = gpu_name();
+  fprintf(f, "{\"gpu\": \"%s\", \"entries\": [\n", gpu.c_str());
+  bool first = true;
+  for (const auto &kv : g_cache) {
+    const auto &c = kv.second.choice;
+    fprintf(f, "%s  {\"N\": %d, \"direction\": %d, \"precision\": %d, \"path\": %d, \"P\": %d, "
+               "\"TB\": %d, \"n1\": %d, \"twm\": %d, \"ctas_per_sm\": %d, \"slabs\": %d, "
+               "\"radix\": [",
+            first ? "" : ",\n", kv.first.N, kv.first.dir, kv.first.prec, c.path, c.P, c.TB, c.n1,
+            c.twm, c.ctas_per_sm, c.slabs);
+    for (int i = 0; i < c.npass; ++i) fprintf(f, "%s%d", i ? ", " : "", c.radix[i]);
+    fprintf(f, "], \"us\": %.3f, \"batch\": %lld}", kv.second.us, (long long)kv.second.batch);
+    first = false;
+  }
+  fprintf(f, "\n]}\n");
+  fclose(f);
+  return FFT_OK;
+}
+
+// Minimal reader for the format write_json produces.
+bool read_int(const std::string &s, const char *key, size_t from, size_t to, int *out) {
+  std::string k = std::string("\"") + key + "\":";
+  size_t p = s.find(k, from);
+  if (p == std::string::npos || p >= to) return false;
+  *out = atoi(s.c_str() + p + k.size());
+  return true;
+}
+
+fft_status_t load_json(const char *path) {
+  FILE *f = fopen(path, "r");
+  if (!f) return FFT_ERR_INVALID_VALUE;
+  std::string s;
+  char buf[4096];
+  size_t n;
+  while ((n = fread(buf, 1, sizeof(buf), f)) > 0) s.append(buf, n);
+  fclose(f);
+  const std::string gpu = gpu_name();
+  size_t g = s.find("\"gpu\": \"");
+  if (g == std::string::npos) return FFT_ERR_INVALID_VALUE;
+  size_t ge = s.find('"', g + 8);
+  if (s.substr(g + 8, ge - (g + 8)) != gpu) return FFT_OK;  // other GPU: ignore
+  size_t pos = s.find("\"entries\"");
+  while (pos != std::string::npos) {
+    size_t b = s.find('{', pos + 1);
+    if (b == std::string::npos) break;
+    size_t e = s.find('}', b);
+    if (e == std::string::npos) break;
+    Key k;
+    Entry en{};
+    bool ok = read_int(s, "N", b, e, &k.N) && read_int(s, "direction", b, e, &k.dir) &&
+              read_int(s, "precision", b, e, &k.prec) &&
+              read_int(s, "path", b, e, &en.choice.path) && read_int(s, "P", b, e, &en.choice.P) &&
+              read_int(s, "TB", b, e, &en.choice.TB) && read_int(s, "n1", b, e, &en.choice.n1) &&
+              read_int(s, "twm", b, e, &en.choice.twm) &&
+              read_int(s, "ctas_per_sm", b, e, &en.choice.ctas_per_sm) &&
+              read_int(s, "slabs", b, e, &en.choice.slabs);
+    size_t r = s.find("\"radix\": [", b);
+    if (ok && r != std::string::npos && r < e) {
+      const char *q = s.c_str() + r + 10;
+      en.choice.npass = 0;
+      while (*q && *q != ']' && en.choice.npass < 8) {
+        en.choice.radix[en.choice.npass++] = (int)strtol(q, (char **)&q, 10);
+        while (*q == ',' || *q == ' ') ++q;
+      }
+      g_cache[k] = en;
+    }
+    pos = e;
+  }
+  return FFT_OK;
+}
+
+}  // namespace
+
+bool tune_lookup(int N, int direction, int precision, TuneChoice *out) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_env_loaded) {
+    g_env_loaded = true;
+    const char *p = getenv("FFTGB_AUTOTUNE_CACHE");
+    if (p && *p) load_json(p);
+  }
+  auto it = g_cache.find(Key{N, direction, precision});
+  if (it == g_cache.end()) return false;
+  *out = it->second.choice;
+  return true;
+}
+
+}  // namespace fftgb
+
+using namespace fftgb;
+
+extern "C" {
+
+fft_status_t fft_autotune(int N, int direction, int precision, int64_t batch,
+                          const char *cache_path) {
+  if (N < 2 || N > 16384 || (N & (N - 1))) return FFT_ERR_INVALID_SIZE;
+  if (direction != FFT_FORWARD && direction != FFT_INVERSE) return FFT_ERR_INVALID_VALUE;
+  if (precision != FFT_PREC_FP32) return FFT_ERR_NOT_SUPPORTED;
+  if (batch < 0) return FFT_ERR_INVALID_SIZE;
+  if (batch == 0) batch = std::max<int64_t>(1, (int64_t(1) << 25) / N);
+  const int ncfg = fft_list_configs(N, nullptr, 0);
+  std::vector<fft_config_t> cfgs(ncfg);
+  fft_list_configs(N, cfgs.data(), ncfg);
+  float2 *in = nullptr, *out = nullptr;
+  const size_t bytes = sizeof(float2) * (size_t)N * (size_t)batch;
+  if (cudaMalloc(&in, bytes) != cudaSuccess || cudaMalloc(&out, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(in);
+    return FFT_ERR_ALLOC;
+  }
+  const int64_t n = (int64_t)N * batch;
+  fill_pattern<<<(unsigned)((n + 255) / 256), 256>>>(in, n);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  fft_status_t result = FFT_OK;
+  double best_us = 1e30;
+  TuneChoice best{};
+  for (const auto &c : cfgs) {
+    fft_plan_t p = nullptr;
+    fft_status_t s = fft_plan_config(&p, N, batch, direction, FFT_FLAG_NO_AUTOTUNE_CACHE, &c);
+    if (s == FFT_ERR_ALLOC) continue;  // e.g. four-step scratch does not fit: skip
+    if (s != FFT_OK) {
+      result = s;
+      break;
+    }
+    for (int w = 0; w < 2 && s == FFT_OK; ++w) s = fft_exec(p, in, out, nullptr);
+    std::vector<float> t;
+    for (int r = 0; r < 7 && s == FFT_OK; ++r) {
+      cudaEventRecord(e0);
+      s = fft_exec(p, in, out, nullptr);
+      cudaEventRecord(e1);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      t.push_back(ms);
+    }
+    fft_destroy(p);
+    if (s != FFT_OK) {
+      result = s;
+      break;
+    }
+    std::sort(t.begin(), t.end());
+    const double us = 1e3 * t[t.size() / 2];
+    if (us < best_us) {
+      best_us = us;
+      best.path = c.path;
+      best.P = c.points_per_thread;
+      best.TB = c.transforms_per_cta;
+      best.npass = c.num_passes;
+      for (int i = 0; i < 8; ++i) best.radix[i] = c.radix[i];
+      best.n1 = c.n1;
+      best.twm = c.twiddle_mode;
+      best.ctas_per_sm = c.ctas_per_sm;
+      best.slabs = c.tma_slabs;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(in);
+  cudaFree(out);
+  if (result != FFT_OK) return result;
+  if (cudaGetLastError() != cudaSuccess) return FFT_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_cache[Key{N, direction, precision}] = Entry{best, best_us, batch};
+  if (cache_path) return write_json(cache_path);
+  return FFT_OK;
+}
+
+fft_status_t fft_autotune_load(const char *cache_path) {
+  if (!cache_path) return FFT_ERR_INVALID_VALUE;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_env_loaded = true;
+  return load_json(cache_path);
+}
+
+fft_status_t fft_autotune_clear(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_cache.clear();
+  g_env_loaded = true;
+  return FFT_OK;
+}
+
+}  // extern "C"

@@ -2,6 +2,7 @@
 #pragma once
 #include "column.cuh"
 #include "registry.h"
+#include "staged.cuh"
 #include "stockham.cuh"
 
 namespace fftgb {
@@ -13,7 +14,7 @@ inline void fill_radix(KernelEntry &e) {
   e.tw_total = SC::tw_total();
 }
 
-template <int N, int P, int TB, int DEF, class SC>
+template <int N, int P, int TB, int TWM, int DEF, class SC>
 inline KernelEntry stockham_entry() {
   KernelEntry e{};
   e.kind = KIND_STOCKHAM;
@@ -25,8 +26,28 @@ inline KernelEntry stockham_entry() {
   fill_radix<SC>(e);
   e.is_default = DEF;
   e.variant = 0;
-  e.fn[0] = (const void *)&stockham_kernel<N, P, TB, -1, SC>;
-  e.fn[1] = (const void *)&stockham_kernel<N, P, TB, +1, SC>;
+  e.twm = TWM;
+  e.fn[0] = (const void *)&stockham_kernel<N, P, TB, -1, SC, TWM>;
+  e.fn[1] = (const void *)&stockham_kernel<N, P, TB, +1, SC, TWM>;
+  return e;
+}
+
+template <int N, int P, int C, int TWM, int DEF, class SC>
+inline KernelEntry staged_entry() {
+  KernelEntry e{};
+  e.kind = KIND_STAGED;
+  e.N = N;
+  e.P = P;
+  e.TB = 1;
+  e.threads = N / P;
+  e.smem = staged_smem_bytes<N, P, C>();
+  fill_radix<SC>(e);
+  e.is_default = DEF;
+  e.variant = 0;
+  e.twm = TWM;
+  e.slabs = C;
+  e.fn[0] = (const void *)&staged_kernel<N, P, C, -1, SC, TWM>;
+  e.fn[1] = (const void *)&staged_kernel<N, P, C, +1, SC, TWM>;
   return e;
 }
 
@@ -51,10 +72,21 @@ inline KernelEntry column_entry() {
 
 #define FFTGB_CAT2(a, b) a##b
 #define FFTGB_CAT(a, b) FFTGB_CAT2(a, b)
-// FFTGB_STOCKHAM(N, P, TB, is_default, radices...)
+// FFTGB_STOCKHAM(N, P, TB, is_default, radices...): registers the kernel in
+// both twiddle modes; `is_default` marks which mode (1 or 2 = TWM + 1) is the
+// built-in choice (0: neither).
 #define FFTGB_STOCKHAM(N, P, TB, DEF, ...)                                   \
   static ::fftgb::Registrar FFTGB_CAT(fftgb_reg_, __COUNTER__)(              \
-      ::fftgb::stockham_entry<N, P, TB, DEF, ::fftgb::Sched<__VA_ARGS__>>())
+      ::fftgb::stockham_entry<N, P, TB, 0, DEF == 1, ::fftgb::Sched<__VA_ARGS__>>()); \
+  static ::fftgb::Registrar FFTGB_CAT(fftgb_reg_, __COUNTER__)(              \
+      ::fftgb::stockham_entry<N, P, TB, 1, DEF == 2, ::fftgb::Sched<__VA_ARGS__>>())
+// FFTGB_STAGED(N, P, C, is_default, radices...): TMA-staged kernel with a
+// ring of C slabs, both twiddle modes (is_default as for FFTGB_STOCKHAM).
+#define FFTGB_STAGED(N, P, C, DEF, ...)                                      \
+  static ::fftgb::Registrar FFTGB_CAT(fftgb_reg_, __COUNTER__)(              \
+      ::fftgb::staged_entry<N, P, C, 0, DEF == 1, ::fftgb::Sched<__VA_ARGS__>>()); \
+  static ::fftgb::Registrar FFTGB_CAT(fftgb_reg_, __COUNTER__)(              \
+      ::fftgb::staged_entry<N, P, C, 1, DEF == 2, ::fftgb::Sched<__VA_ARGS__>>())
 // FFTGB_COLUMN(L, P, C, variant, is_default, radices...)
 #define FFTGB_COLUMN(L, P, C, VAR, DEF, ...)                                 \
   static ::fftgb::Registrar FFTGB_CAT(fftgb_reg_, __COUNTER__)(              \

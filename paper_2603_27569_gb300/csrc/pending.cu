@@ -3,7 +3,6 @@
 #include "plan.h"
 
 namespace fftgb {
-bool tune_lookup(int, int, int, TuneChoice *) { return false; }
 fft_status_t tc_plan(fft_plan_impl *) { return FFT_ERR_NOT_SUPPORTED; }
 fft_status_t tc_exec(fft_plan_impl *, const float2 *, float2 *, int64_t, cudaStream_t) {
   return FFT_ERR_NOT_SUPPORTED;
@@ -21,9 +20,6 @@ fft_status_t fft_ragged_plan(fft_plan_t *out, int, const int *, const int *, con
   if (out) *out = nullptr;
   return FFT_ERR_NOT_SUPPORTED;
 }
-fft_status_t fft_autotune(int, int, int, int64_t, const char *) { return FFT_ERR_NOT_SUPPORTED; }
-fft_status_t fft_autotune_load(const char *) { return FFT_ERR_NOT_SUPPORTED; }
-fft_status_t fft_autotune_clear(void) { return FFT_OK; }
 fft_status_t fft_spectral_filter_fused(const void *, const void *, void *, int, int64_t, int,
                                        void *) {
   return FFT_ERR_NOT_SUPPORTED;

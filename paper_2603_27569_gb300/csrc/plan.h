@@ -33,6 +33,8 @@ struct fft_plan_impl {
   int device = 0;
   // single-CTA path
   const KernelEntry *k_single = nullptr;
+  int ctas_per_sm = 0;    // 0: one CTA per tile; > 0 persistent grid
+  int64_t grid_ctas = 0;  // persistent grid size (0 = one CTA per tile)
   // four-step path: phase-1 and phase-2 column kernels, split N = n1 * n2
   const KernelEntry *k_col1 = nullptr, *k_col2 = nullptr;
   int n1 = 0, n2 = 0;
@@ -60,11 +62,14 @@ struct fft_plan_impl {
 fft_status_t cuda_status(cudaError_t e);
 fft_status_t build_twiddles(fft_plan_impl *pl, const std::vector<TwSeg> &segs);
 std::vector<TwSeg> pass_segments(const KernelEntry &k, int64_t &offset);
-const KernelEntry *find_stockham(int N, int P, int TB, const int *radix, int npass);
+const KernelEntry *find_stockham(int N, int P, int TB, const int *radix, int npass, int twm);
 const KernelEntry *default_stockham(int N);
 const KernelEntry *default_column(int L, int variant);
 fft_status_t launch_stockham(const KernelEntry *k, int dir, const float2 *in, float2 *out,
-                             const float2 *tw, int64_t rows, float scale, cudaStream_t st);
+                             const float2 *tw, int64_t rows, float scale, int64_t grid_cap,
+                             cudaStream_t st);
+// Persistent grid for kernel k with `per_sm` CTAs per SM (-1: occupancy).
+int64_t persistent_grid(const KernelEntry *k, int per_sm);
 fft_status_t exec_rows(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t rows,
                        cudaStream_t st);
 fft_status_t ensure_smem_attr(const KernelEntry *k);
@@ -76,6 +81,9 @@ struct TuneChoice {
   int P, TB, npass;
   int radix[8];
   int n1;                   // four-step split (n1)
+  int twm;                  // twiddle mode
+  int ctas_per_sm;          // 0 / -1 / k (see fft_config_t)
+  int slabs;                // TMA-staged ring size (0: direct loads)
 };
 bool tune_lookup(int N, int direction, int precision, TuneChoice *out);
 

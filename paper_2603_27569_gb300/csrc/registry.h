@@ -8,7 +8,7 @@
 
 namespace fftgb {
 
-enum KernelKind { KIND_STOCKHAM = 1, KIND_COLUMN = 2 };
+enum KernelKind { KIND_STOCKHAM = 1, KIND_COLUMN = 2, KIND_STAGED = 3 };
 
 struct KernelEntry {
   int kind;
@@ -22,6 +22,8 @@ struct KernelEntry {
   int tw_total;   // entries of the per-pass twiddle tables
   int is_default; // the built-in choice for this (kind, N, variant)
   int variant;    // column kernels: 0 plain, 1 twiddle + transposed store
+  int twm;        // twiddle mode: 0 all from tables, 1 rows 1/4(/16) + products
+  int slabs;      // staged kernels: slabs held in the TMA ring (0 otherwise)
   const void *fn[2];  // [0] forward (D = -1), [1] inverse (D = +1)
 };
 

@@ -63,8 +63,46 @@ struct StockhamArgs {
   float scale;          // applied at the final store (1 or 1/N)
 };
 
+// Is row j of a pass table loaded (twiddle mode 1) rather than derived?
+template <int r>
+__host__ __device__ constexpr bool tw_loaded(int j) {
+  return j == 1 || (r == 4 && j == 2) || (r >= 8 && j == 4) || (r == 32 && j == 16);
+}
+
+// The r - 1 twiddles W^{j k}, j = 1 .. r-1, of one butterfly.
+//   TWM = 0: every one read from the pass table (row j - 1).
+//   TWM = 1: rows 1, 4 (and 2 for r = 4, 16 for r = 32) read; the others
+//            formed as products W^{j k} = W^{a k} W^{b k}, a + b = j, along a
+//            tree of depth <= 3 (<= 4 for r = 32).  This trades r - 3 table
+//            reads (L1 traffic) for as many complex multiplies.
+template <int r, int p, int TWM>
+__device__ __forceinline__ void load_twiddles(float2 (&w)[r], const float2 *__restrict__ tws, int k) {
+  if constexpr (TWM == 0) {
+#pragma unroll
+    for (int j = 1; j < r; ++j) w[j] = __ldg(tws + (j - 1) * p + k);
+  } else {
+#pragma unroll
+    for (int j = 1; j < r; ++j)
+      if (tw_loaded<r>(j)) w[j] = __ldg(tws + (j - 1) * p + k);
+#pragma unroll
+    for (int j = 2; j < r; ++j) {
+      if (tw_loaded<r>(j)) continue;
+      if (j < 4) {
+        w[j] = cmul(w[j - 1], w[1]);               // w2 = w1 w1, w3 = w2 w1
+      } else if (j % 4 == 0) {
+        // w8 = w4 w4, w12 = w8 w4, w20 = w16 w4, w24 = w16 w8, w28 = w24 w4
+        const int a = (j >= 16 && r == 32) ? 16 : 4 * ((j / 4) / 2);
+        w[j] = cmul(w[a], w[j - a]);
+      } else {
+        const int base = j & ~3;                   // w_{4a+b} = w_{4a} w_b
+        w[j] = cmul(w[base], w[j - base]);
+      }
+    }
+  }
+}
+
 // Twiddle + butterflies of pass S for every butterfly q of this thread.
-template <int N, int P, int D, class SC, int S>
+template <int N, int P, int D, class SC, int S, int TWM>
 __device__ __forceinline__ void pass_compute(float2 (&a)[P], int lt, const float2 *__restrict__ tw) {
   constexpr int r = SC::radix[S];
   constexpr int p = SC::stride(S);
@@ -76,11 +114,10 @@ __device__ __forceinline__ void pass_compute(float2 (&a)[P], int lt, const float
     for (int q = 0; q < Q; ++q) {
       const int i = lt + q * T;
       const int k = i & (p - 1);
+      float2 w[r];
+      load_twiddles<r, p, TWM>(w, tws, k);
 #pragma unroll
-      for (int j = 1; j < r; ++j) {
-        float2 w = __ldg(tws + (j - 1) * p + k);
-        a[q + j * Q] = cmul_dir<D>(a[q + j * Q], w);
-      }
+      for (int j = 1; j < r; ++j) a[q + j * Q] = cmul_dir<D>(a[q + j * Q], w[j]);
     }
   }
 #pragma unroll
@@ -138,16 +175,16 @@ __device__ __forceinline__ void pass_read(float2 (&a)[P], int lt, const float2 *
 
 // Passes S .. npass-1.  On entry a[] holds pass S's inputs.  On return a[]
 // holds the final outputs of the last pass in its butterfly order.
-template <int N, int P, int D, class SC, int S, class LY>
+template <int N, int P, int D, class SC, int S, class LY, int TWM = 0>
 __device__ __forceinline__ void run_passes(float2 (&a)[P], int lt, float2 *buf,
                                            const float2 *__restrict__ tw, const LY &ly) {
-  pass_compute<N, P, D, SC, S>(a, lt, tw);
+  pass_compute<N, P, D, SC, S, TWM>(a, lt, tw);
   if constexpr (S + 1 < SC::npass) {
     if constexpr (S > 0) __syncthreads();  // every read of the buffer is done
     pass_write<N, P, SC, S>(a, lt, buf, ly);
     __syncthreads();
     pass_read<N, P, SC, S>(a, lt, buf, ly);
-    run_passes<N, P, D, SC, S + 1>(a, lt, buf, tw, ly);
+    run_passes<N, P, D, SC, S + 1, LY, TWM>(a, lt, buf, tw, ly);
   }
 }
 
@@ -162,7 +199,23 @@ __device__ __forceinline__ int final_index(int lt, int m) {
   return lt + q * T + j * (N / r);
 }
 
-template <int N, int P, int TB, int D, class SC>
+// L2 prefetch of `bytes` (a multiple of 16) starting at p, issued by the 32
+// lanes of one warp, each for its slice, through the bulk-copy (TMA) engine.
+__device__ __forceinline__ void prefetch_l2_warp(const void *p, long long bytes, int lane) {
+  const long long chunk = (((bytes + 31) / 32) + 15) & ~15ll;
+  const long long off = lane * chunk;
+  if (off < bytes) {
+    const long long n = bytes - off < chunk ? bytes - off : chunk;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
+                 :: "l"((const char *)p + off), "r"((unsigned)n) : "memory");
+  }
+}
+
+// Persistent over tiles of TB rows: CTA c handles tiles c, c + G, c + 2G, ...
+// (G = gridDim.x; a grid of one CTA per tile runs the loop once).  Before a
+// tile's loads, warp 0 asks the bulk-copy engine to prefetch the CTA's NEXT
+// tile into L2, so HBM streams the next rows while this tile computes.
+template <int N, int P, int TB, int D, class SC, int TWM>
 __global__ void __launch_bounds__(TB *(N / P))
 stockham_kernel(StockhamArgs args) {
   static_assert(SC::product() == N, "radix schedule must multiply to N");
@@ -171,24 +224,41 @@ stockham_kernel(StockhamArgs args) {
   extern __shared__ float2 smem[];
   const int b = threadIdx.x / T;
   const int lt = threadIdx.x - b * T;
-  const long long row = (long long)blockIdx.x * TB + b;
-  const bool active = row < args.batch;
   float2 *buf = smem + b * N;
-  float2 a[P];
-  const float2 *src = args.in + row * N;
-  if (active) {
+  const long long ntiles = (args.batch + TB - 1) / TB;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long next = tile + gridDim.x;
+    if (next < ntiles && threadIdx.x < 32) {
+      const long long rows = args.batch - next * TB < TB ? args.batch - next * TB : TB;
+      prefetch_l2_warp(args.in + next * TB * N, rows * N * (long long)sizeof(float2),
+                       threadIdx.x);
+    }
+    const long long row = tile * TB + b;
+    const bool active = row < args.batch;
+    float2 a[P];
+    const float2 *src = args.in + row * N;
+    if (active) {
 #pragma unroll
-    for (int m = 0; m < P; ++m) a[m] = __ldg(src + lt + m * T);
-  } else {
+      for (int m = 0; m < P; ++m) a[m] = __ldcs(src + lt + m * T);
+    } else {
 #pragma unroll
-    for (int m = 0; m < P; ++m) a[m] = make_float2(0.f, 0.f);
-  }
-  run_passes<N, P, D, SC, 0>(a, lt, buf, args.tw, SwizzledRow{});
-  if (active) {
-    float2 *dst = args.out + row * N;
-    const float s = args.scale;
+      for (int m = 0; m < P; ++m) a[m] = make_float2(0.f, 0.f);
+    }
+    // Opaque per tile: keeps the compiler from hoisting the loop-invariant
+    // twiddle reads and exchange addresses out of the tile loop into
+    // (occupancy-costly) registers.
+    const float2 *twp = args.tw;
+    float2 *bufp = buf;
+    int ltp = lt;
+    asm volatile("" : "+l"(twp), "+l"(bufp), "+r"(ltp));
+    run_passes<N, P, D, SC, 0, SwizzledRow, TWM>(a, ltp, bufp, twp, SwizzledRow{});
+    if (active) {
+      float2 *dst = args.out + row * N;
+      const float s = args.scale;
 #pragma unroll
-    for (int m = 0; m < P; ++m) dst[final_index<N, P, SC>(lt, m)] = cscale(a[m], s);
+      for (int m = 0; m < P; ++m) __stcs(dst + final_index<N, P, SC>(ltp, m), cscale(a[m], s));
+    }
+    if (next < ntiles) __syncthreads();  // the next tile rewrites the buffer
   }
 }
 
