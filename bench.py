@@ -227,6 +227,13 @@ def run_ours(args):
         torch.distributed.barrier()
     fg.lib()
 
+    # Autotune every (N, direction) on this GPU before anything is timed: the
+    # plans below then use the fastest compiled configuration.
+    if not args.no_autotune:
+        for N in SIZES:
+            for d in (fg.FFT_FORWARD, fg.FFT_INVERSE):
+                fg.fft_autotune(N, d, 0, POINTS // N)
+
     # Inputs: one 2^25-point N(0,1) buffer (seed 0), viewed as [2^25/N, N].
     x = torch.from_numpy(synth.gaussian(POINTS, seed=0)).to(dev)
     y = torch.empty_like(x)
@@ -296,12 +303,15 @@ def run_ours(args):
             "fwd_frac_hbm": round(gbs_f / peak, 4), "inv_frac_hbm": round(gbs_i / peak, 4),
             "path": {1: "single_cta", 2: "fourstep"}.get(info["path"], info["path"]),
             "radix": info["radix"], "points_per_thread": info["points_per_thread"],
+            "twiddle_mode": info["twiddle_mode"], "grid_ctas": info["grid_ctas"],
+            "tma_slabs": info["tma_slabs"], "n1": info["n1"],
         }
     dom = max(keys, key=lambda k: per_key_ms[k])
     dom_ms = per_key_ms[dom]
     dom_info = plans[dom].info()
-    kname = (f"{'stockham' if dom_info['path'] == 1 else 'fourstep'}_N{dom[0]}_"
-             f"{'fwd' if dom[1] < 0 else 'inv'}")
+    kind = ("staged" if dom_info["tma_slabs"] else "stockham") if dom_info["path"] == 1 \
+        else "fourstep"
+    kname = f"{kind}_N{dom[0]}_{'fwd' if dom[1] < 0 else 'inv'}"
     achieved = 16.0 * POINTS / (dom_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic_for(kname),
@@ -407,6 +417,29 @@ def bench_fwd_bwd(fg, synth, torch, dev, per_key_ms):
             "gflops_equiv": round(4 * flops(N, rows) / (fb_ms * 1e-3) / 1e9, 1)}
 
 
+def run_profile_case(args):
+    """A small fixed case for ncu: one plan of the sweep's size at N, executed
+    three times (capture the third launch with -s 2 -c 1)."""
+    import torch
+
+    import paper_2603_27569_gb300 as fg
+    from paper_2603_27569_gb300 import build as fbuild
+
+    fbuild.build()
+    N = args.profile_case
+    batch = POINTS // N            # 256 MiB in: larger than L2
+    x = torch.randn(batch * N, dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    cfg = json.loads(args.profile_config) if args.profile_config else None
+    p = fg.Plan(N, batch, fg.FFT_FORWARD, flags=args.profile_flags, config=cfg)
+    for _ in range(3):
+        p(x, out=y)
+    torch.cuda.synchronize()
+    print("profile case ok", N, p.info(), flush=True)
+    p.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -419,7 +452,16 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the built-in configurations instead of autotuning first")
+    ap.add_argument("--profile-case", type=int, default=0,
+                    help="run one N of the sweep three times (for ncu) and exit")
+    ap.add_argument("--profile-flags", type=int, default=0)
+    ap.add_argument("--profile-config", type=str, default="",
+                    help="JSON of one fft_list_configs entry to force")
     args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -276,8 +276,10 @@ fft_status_t exec_rows(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t
 
 static bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 
-// Built-in launch shape of the single-CTA path: persistent at full occupancy.
-constexpr int kDefaultCtasPerSm = -1;
+// Built-in launch shape of the single-CTA path: one CTA per tile (measured
+// faster than the persistent shape for every N up to 8192 on GB300; the
+// staged kernels used at N = 16384 are persistent by construction).
+constexpr int kDefaultCtasPerSm = 0;
 
 // Four-step split N = n1 * n2 with both factors column-kernel lengths (16..256).
 static bool fourstep_split(int N, int want_n1, int *n1, int *n2) {
