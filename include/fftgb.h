@@ -256,6 +256,32 @@ fft_status_t fft_filter_grad_h(const void *X, const void *G, void *grad_H, int N
 fft_status_t fft_spectral_filter_fused(const void *x, const void *H, void *y, int N,
                                        int64_t batch, int adjoint, void *stream);
 
+/*
+ * fft_fourstep_noalloc — the two-phase four-step transform (same kernels and
+ * results as a plan made with FFT_FLAG_FORCE_FOURSTEP) for callers that must
+ * not allocate device memory.  The paper has no counterpart: this entry
+ * point exists for users of the library whose code may not call cudaMalloc
+ * while it runs, e.g. a real-time pipeline whose memory is fixed at start-up
+ * or code that hands the device heap to its own allocator.  It takes no plan
+ * (making a plan allocates) and allocates nothing: its intermediate lives in
+ * a fixed file-scope device array of FFT_NOALLOC_MAX_POINTS complex values
+ * (16 MiB) and its twiddle tables in another (512 KiB); both are reserved on
+ * every GPU that loads the library until the process exits.
+ * in, out: device pointers to batch*N float2 (layout as above), 16-byte
+ * aligned; in == out allowed.  N: power of two in [256, 16384].
+ * N * batch above FFT_NOALLOC_MAX_POINTS is FFT_ERR_INVALID_SIZE (split
+ * larger batches into several calls).  direction: FFT_FORWARD or
+ * FFT_INVERSE (inverse scaled by 1/N).  Asynchronous on `stream`.
+ * The first call on a device sets that device up (resolves the arrays'
+ * addresses, fills the tables, synchronises the device): make it before any
+ * stream capture.  All calls share the one scratch array, which keeps the
+ * last call's contents; calls whose work overlaps on the GPU race with each
+ * other, so serialise them (e.g. one stream).
+ */
+#define FFT_NOALLOC_MAX_POINTS 2097152
+fft_status_t fft_fourstep_noalloc(const void *in, void *out, int N, int64_t batch,
+                                  int direction, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

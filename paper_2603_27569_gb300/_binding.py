@@ -23,6 +23,7 @@ __all__ = [
     "fft_autotune_load", "fft_autotune_clear", "fft_filter_apply",
     "fft_filter_grad_h_workspace", "fft_filter_grad_h", "fft_spectral_filter_fused",
     "PlanInfo", "Config", "EXPORTED_SYMBOLS", "fft_list_configs", "fft_plan_config",
+    "fft_fourstep_noalloc", "FFT_NOALLOC_MAX_POINTS",
 ]
 
 FFT_FORWARD = -1
@@ -34,6 +35,7 @@ FFT_FLAG_FORCE_FOURSTEP = 0x4
 FFT_FLAG_NO_AUTOTUNE_CACHE = 0x8
 FFT_FLAG_ADJOINT = 0x10
 FFT_PATH_SINGLE_CTA, FFT_PATH_FOURSTEP, FFT_PATH_RAGGED, FFT_PATH_TENSORCORE = 1, 2, 3, 4
+FFT_NOALLOC_MAX_POINTS = 2097152
 
 STATUS = {
     0: "FFT_OK", 1: "FFT_ERR_INVALID_SIZE", 2: "FFT_ERR_INVALID_VALUE", 3: "FFT_ERR_MISALIGNED",
@@ -118,6 +120,7 @@ _SIGS = {
     "fft_spectral_filter_fused": ([_vp, _vp, _vp, _i32, _i64, _i32, _vp], _i32),
     "fft_list_configs": ([_i32, _vp, _i32], _i32),
     "fft_plan_config": ([ctypes.POINTER(_vp), _i32, _i64, _i32, _i32, ctypes.POINTER(Config)], _i32),
+    "fft_fourstep_noalloc": ([_vp, _vp, _i32, _i64, _i32, _vp], _i32),
 }
 EXPORTED_SYMBOLS = tuple(_SIGS)
 
@@ -293,3 +296,9 @@ def fft_plan_config(N: int, batch: int, direction: int, config: dict, flags: int
     _check(lib().fft_plan_config(ctypes.byref(h), N, batch, direction, flags, ctypes.byref(c)),
            "fft_plan_config")
     return h.value
+
+
+def fft_fourstep_noalloc(inp, out, N: int, batch: int, direction: int, stream=None) -> None:
+    """Four-step transform that allocates nothing (fixed device scratch)."""
+    _check(lib().fft_fourstep_noalloc(_ptr(inp), _ptr(out), N, batch, direction,
+                                      _stream(stream)), "fft_fourstep_noalloc")
