@@ -50,9 +50,25 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def source_hash() -> str:
+# Source files that define each kernel family (the traffic a profile recorded
+# stays valid while these are unchanged).
+KERNEL_SOURCES = {
+    "stockham": ["butterfly.cuh", "stockham.cuh", "instantiate.cuh", "registry.h",
+                 "k_small.cu", "k_mid.cu", "k_4096.cu", "k_large.cu"],
+    "staged": ["butterfly.cuh", "stockham.cuh", "staged.cuh", "instantiate.cuh", "registry.h",
+               "k_staged.cu"],
+    "fourstep": ["butterfly.cuh", "stockham.cuh", "column.cuh", "instantiate.cuh", "registry.h",
+                 "k_column.cu"],
+}
+
+
+def source_hash(kind: str | None = None) -> str:
+    """sha256 prefix of one kernel family's sources (or of all of csrc/)."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2603_27569_gb300", "csrc", "*"))):
+    d = os.path.join(ROOT, "paper_2603_27569_gb300", "csrc")
+    files = ([os.path.join(d, f) for f in KERNEL_SOURCES[kind]] if kind
+             else sorted(glob.glob(os.path.join(d, "*"))))
+    for f in files:
         h.update(open(f, "rb").read())
     return h.hexdigest()[:16]
 
@@ -133,7 +149,7 @@ def traffic_for(kernel_key: str):
         return None
     d = json.load(open(p))
     e = d.get(kernel_key)
-    if not e or e.get("source_hash") != source_hash():
+    if not e or e.get("source_hash") != source_hash(kernel_key.split("_")[0]):
         return None
     return e.get("dram_bytes_per_launch")
 
