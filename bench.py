@@ -367,6 +367,7 @@ def run_ours(args):
     extras = {}
     if not args.no_extras and rank == 0:
         extras["fwd_bwd"] = bench_fwd_bwd(fg, synth, torch, dev, per_key_ms)
+        extras["ragged"] = bench_ragged(fg, synth, torch, dev)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nthreads = os.cpu_count() or 1
@@ -395,6 +396,65 @@ def run_ours(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def bench_ragged(fg, synth, torch, dev):
+    """20000 mixed transforms (log2 N ~ U{8..14}, mixed directions, seed 0) in
+    one persistent launch (CUDA graph) vs one plain launch per (N, direction)
+    group over the same transforms gathered contiguously (gathering untimed)."""
+    import numpy as np
+
+    d = synth.ragged_draw(20000, seed=0)
+    total = d["total"]
+    x = torch.from_numpy(synth.gaussian(total, seed=0)).to(dev)
+    y = torch.empty_like(x)
+    plan = fg.fft_ragged_plan(d["N"], d["direction"], d["offset"], d["offset"])
+    st = torch.cuda.current_stream(dev)
+    flop = sum(5.0 * int(n) * math.log2(int(n)) for n in d["N"])
+    for _ in range(3):
+        fg.fft_exec(plan, x, y, st)
+    torch.cuda.synchronize()
+    reps = 10
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(reps):
+        fg.fft_exec(plan, x, y, st)
+    b.record(st)
+    torch.cuda.synchronize()
+    rag_ms = a.elapsed_time(b) / reps
+    fg.fft_destroy(plan)
+    # plain baseline: one plan per (N, direction) over contiguous groups
+    groups = []
+    for N in np.unique(d["N"]):
+        for dirn in (-1, 1):
+            sel = np.nonzero((d["N"] == N) & (d["direction"] == dirn))[0]
+            if len(sel):
+                groups.append((int(N), dirn, len(sel)))
+    bufs = [(torch.empty(N * c, dtype=torch.complex64, device=dev),
+             torch.empty(N * c, dtype=torch.complex64, device=dev),
+             fg.Plan(N, c, dirn, device=dev)) for N, dirn, c in groups]
+    for gi, go, p in bufs:
+        gi.copy_(x[: gi.numel()])
+    for _ in range(3):
+        for gi, go, p in bufs:
+            p(gi, out=go)
+    torch.cuda.synchronize()
+    a.record(st)
+    for _ in range(reps):
+        for gi, go, p in bufs:
+            p(gi, out=go)
+    b.record(st)
+    torch.cuda.synchronize()
+    plain_ms = a.elapsed_time(b) / reps
+    for _, _, p in bufs:
+        p.close()
+    return {"workload": "20000 transforms, log2 N ~ U{8..14}, mixed fwd/inv, N(0,1) seed 0, "
+                        "packed in draw order",
+            "bytes": 16 * total, "ragged_ms": round(rag_ms, 4), "plain_ms": round(plain_ms, 4),
+            "plain_launches": len(groups),
+            "ragged_gflops": round(flop / (rag_ms * 1e-3) / 1e9, 1),
+            "plain_gflops": round(flop / (plain_ms * 1e-3) / 1e9, 1),
+            "ragged_vs_plain": round(plain_ms / rag_ms, 3)}
 
 
 def bench_fwd_bwd(fg, synth, torch, dev, per_key_ms):

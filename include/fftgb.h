@@ -204,12 +204,17 @@ fft_status_t fft_twiddle_index(fft_plan_t plan, int64_t pos, int64_t *M, int64_t
  * fft_ragged_plan — a batch of `count` transforms of mixed lengths and
  * directions, executed in ONE persistent launch (longest transforms first,
  * work claimed through a device counter).
- * N[i]: power of two in [2, 16384]; direction[i]: -1 or +1;
+ * N[i]: power of two in [16, 16384] (2..8 give FFT_ERR_NOT_SUPPORTED);
+ * direction[i]: -1 or +1;
  * in_offset[i], out_offset[i]: start of transform i, in complex elements,
  * inside the packed buffers passed to fft_exec(); every offset must be a
  * multiple of 2 (16-byte alignment).  Host arrays are copied; the caller keeps
- * ownership.  flags: FFT_FLAG_UNNORMALIZED_INVERSE and
- * FFT_FLAG_NO_AUTOTUNE_CACHE are honoured.
+ * ownership.  flags: FFT_FLAG_UNNORMALIZED_INVERSE (FFT_FLAG_NO_AUTOTUNE_CACHE
+ * is accepted and has no effect).  Work is claimed longest-first: rows of
+ * 16384 by whole CTAs, rows of 8192 by CTA halves, rows of <= 4096 in
+ * 4096-point units by CTA quarters.  fft_exec replays a CUDA graph (counter
+ * reset + kernel) captured for the (in, out) pair; a new pair re-captures.
+ * Reference: the batched radar FFTs of Sec. II-D with mixed lengths.
  */
 fft_status_t fft_ragged_plan(fft_plan_t *out, int count, const int *N,
                              const int *direction, const int64_t *in_offset,

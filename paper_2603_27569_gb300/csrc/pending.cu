@@ -8,18 +8,9 @@ fft_status_t tc_exec(fft_plan_impl *, const float2 *, float2 *, int64_t, cudaStr
   return FFT_ERR_NOT_SUPPORTED;
 }
 void tc_destroy(fft_plan_impl *) {}
-fft_status_t ragged_exec(fft_plan_impl *, const float2 *, float2 *, cudaStream_t) {
-  return FFT_ERR_NOT_SUPPORTED;
-}
-void ragged_destroy(fft_plan_impl *) {}
 }  // namespace fftgb
 
 extern "C" {
-fft_status_t fft_ragged_plan(fft_plan_t *out, int, const int *, const int *, const int64_t *,
-                             const int64_t *, int) {
-  if (out) *out = nullptr;
-  return FFT_ERR_NOT_SUPPORTED;
-}
 fft_status_t fft_spectral_filter_fused(const void *, const void *, void *, int, int64_t, int,
                                        void *) {
   return FFT_ERR_NOT_SUPPORTED;

@@ -175,16 +175,29 @@ __device__ __forceinline__ void pass_read(float2 (&a)[P], int lt, const float2 *
 
 // Passes S .. npass-1.  On entry a[] holds pass S's inputs.  On return a[]
 // holds the final outputs of the last pass in its butterfly order.
-template <int N, int P, int D, class SC, int S, class LY, int TWM = 0>
+// Barrier policies for the exchanges: the whole CTA, or a named barrier
+// (`bar.sync id, count`) shared by a group of warps working on its own rows.
+struct CtaBarrier {
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+struct NamedBarrier {
+  int id, count;  // id 1..15; count a multiple of 32
+  __device__ __forceinline__ void sync() const {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+  }
+};
+
+template <int N, int P, int D, class SC, int S, class LY, int TWM = 0, class BR = CtaBarrier>
 __device__ __forceinline__ void run_passes(float2 (&a)[P], int lt, float2 *buf,
-                                           const float2 *__restrict__ tw, const LY &ly) {
+                                           const float2 *__restrict__ tw, const LY &ly,
+                                           const BR &br = BR{}) {
   pass_compute<N, P, D, SC, S, TWM>(a, lt, tw);
   if constexpr (S + 1 < SC::npass) {
-    if constexpr (S > 0) __syncthreads();  // every read of the buffer is done
+    if constexpr (S > 0) br.sync();  // every read of the buffer is done
     pass_write<N, P, SC, S>(a, lt, buf, ly);
-    __syncthreads();
+    br.sync();
     pass_read<N, P, SC, S>(a, lt, buf, ly);
-    run_passes<N, P, D, SC, S + 1, LY, TWM>(a, lt, buf, tw, ly);
+    run_passes<N, P, D, SC, S + 1, LY, TWM, BR>(a, lt, buf, tw, ly, br);
   }
 }
 
