@@ -368,6 +368,7 @@ def run_ours(args):
     if not args.no_extras and rank == 0:
         extras["fwd_bwd"] = bench_fwd_bwd(fg, synth, torch, dev, per_key_ms)
         extras["ragged"] = bench_ragged(fg, synth, torch, dev)
+        extras["tensorcore"] = bench_tc(fg, synth, torch, dev)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nthreads = os.cpu_count() or 1
@@ -455,6 +456,47 @@ def bench_ragged(fg, synth, torch, dev):
             "ragged_gflops": round(flop / (rag_ms * 1e-3) / 1e9, 1),
             "plain_gflops": round(flop / (plain_ms * 1e-3) / 1e9, 1),
             "ragged_vs_plain": round(plain_ms / rag_ms, 3)}
+
+
+def bench_tc(fg, synth, torch, dev):
+    """Split-precision tensor-core path (config: N in {4096, 16384}, batch 16384,
+    N(0,1)): throughput vs the plain FP32 plan on the same data, and the
+    relative L2 difference between the two (the error against the FP64 oracle
+    is measured in the tests)."""
+    out = {}
+    for N in (4096, 16384):
+        batch = 16384
+        x = torch.from_numpy(synth.gaussian((batch, N), seed=0)).to(dev)
+        y = torch.empty_like(x)
+        res = {}
+        ref = None
+        for name, prec in (("fp32", fg.FFT_PREC_FP32), ("fp16x2", fg.FFT_PREC_FP16X2),
+                           ("bf16x2", fg.FFT_PREC_BF16X2)):
+            p = fg.Plan(N, batch, fg.FFT_FORWARD, precision=prec, device=dev)
+            for _ in range(3):
+                p(x, out=y)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 10
+            a.record()
+            for _ in range(reps):
+                p(x, out=y)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / reps
+            r = {"ms": round(ms, 4), "gflops": round(flops(N, batch) / (ms * 1e-3) / 1e9, 1),
+                 "frac_hbm": round(16.0 * N * batch / (ms * 1e-3) / 1e9 / peaks()[0], 4)}
+            if ref is None:
+                ref = y.clone()
+            else:
+                d = torch.linalg.vector_norm(y - ref, dim=1) / torch.linalg.vector_norm(ref, dim=1)
+                r["max_rel_l2_vs_fp32_path"] = float(d.max())
+            res[name] = r
+            p.close()
+        res["fp16x2_speedup_vs_fp32"] = round(res["fp32"]["ms"] / res["fp16x2"]["ms"], 3)
+        out[str(N)] = res
+        del x, y, ref
+    return out
 
 
 def bench_fwd_bwd(fg, synth, torch, dev, per_key_ms):

@@ -3,11 +3,6 @@
 #include "plan.h"
 
 namespace fftgb {
-fft_status_t tc_plan(fft_plan_impl *) { return FFT_ERR_NOT_SUPPORTED; }
-fft_status_t tc_exec(fft_plan_impl *, const float2 *, float2 *, int64_t, cudaStream_t) {
-  return FFT_ERR_NOT_SUPPORTED;
-}
-void tc_destroy(fft_plan_impl *) {}
 }  // namespace fftgb
 
 extern "C" {

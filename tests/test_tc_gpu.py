@@ -1,0 +1,70 @@
+"""Split-precision tensor-core FFT against the FP64 oracle.
+
+Target: relative L2 error <= 1e-5 per transform for FP16 hi+lo.  BF16 hi+lo
+keeps ~16 significant bits, so its error is reported as measured (and bounded
+here at 1e-4).  The per-size error table is printed (pytest -s)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2603_27569_gb300 as fg
+from paper_2603_27569_gb300 import synth
+from gpu_util import NTHREADS, TOL_SPLIT, rel_l2_rows, to_dev, to_host
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PREC = {"fp16x2": fg.FFT_PREC_FP16X2, "bf16x2": fg.FFT_PREC_BF16X2}
+BOUND = {"fp16x2": TOL_SPLIT, "bf16x2": 1e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2603_27569_gb300 import build
+
+    build.build()
+
+
+def run_tc(x, direction, prec):
+    N = x.shape[-1]
+    plan = fg.Plan(N, x.shape[0], direction, precision=PREC[prec])
+    assert plan.info()["path"] == fg.FFT_PATH_TENSORCORE
+    y = to_host(plan(to_dev(x)))
+    plan.close()
+    return y
+
+
+@pytest.mark.parametrize("prec", ["fp16x2", "bf16x2"])
+@pytest.mark.parametrize("N", [256, 4096, 16384])
+@pytest.mark.parametrize("dist", ["gaussian", "uniform"])
+@pytest.mark.parametrize("direction", [fg.FFT_FORWARD, fg.FFT_INVERSE])
+def test_split_precision_error_vs_oracle(prec, N, dist, direction):
+    batch = 37
+    x = synth.gaussian((batch, N), seed=0) if dist == "gaussian" else \
+        synth.uniform((batch, N), seed=3)
+    y = run_tc(x, direction, prec)
+    want = oracle.fft(x, inverse=direction > 0, nthreads=NTHREADS)
+    err = rel_l2_rows(y, want)
+    print(f"\nTC {prec} N={N} {dist} {'inv' if direction > 0 else 'fwd'}: "
+          f"max rel L2 {err.max():.3e} median {np.median(err):.3e}")
+    assert err.max() <= BOUND[prec]
+
+
+@pytest.mark.parametrize("N", [4096, 16384])
+def test_config5_batch_sampled_rows(N):
+    # the config's batch (16384 rows); 64 sampled rows checked against the oracle
+    batch = 16384
+    x = synth.gaussian((batch, N), seed=0)
+    y = run_tc(x, fg.FFT_FORWARD, "fp16x2")
+    rng = np.random.Generator(np.random.PCG64(11))
+    rows = np.unique(np.concatenate([[0, batch - 1], rng.integers(0, batch, 62)]))
+    err = rel_l2_rows(y[rows], oracle.fft(x[rows], nthreads=NTHREADS))
+    print(f"\nTC fp16x2 N={N} batch {batch}: sampled max rel L2 {err.max():.3e}")
+    assert err.max() <= TOL_SPLIT
+    assert np.isfinite(y).all()
+
+
+def test_unsupported_sizes_are_refused():
+    with pytest.raises(fg.FFTError) as e:
+        fg.Plan(1024, 4, fg.FFT_FORWARD, precision=fg.FFT_PREC_FP16X2)
+    assert e.value.status == 7
