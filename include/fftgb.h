@@ -77,6 +77,7 @@ typedef enum {
 #define FFT_PATH_FOURSTEP 2    /* column FFTs + twiddle, then row FFTs        */
 #define FFT_PATH_RAGGED 3      /* persistent ragged launch                    */
 #define FFT_PATH_TENSORCORE 4  /* split-precision tensor-core radix-16 DFT    */
+#define FFT_PATH_FILTER 5      /* fused spectral filter (fft_filter_plan)     */
 
 /* What a plan chose; filled by fft_plan_info(). */
 typedef struct {
@@ -244,22 +245,42 @@ fft_status_t fft_autotune_clear(void);
  *   X[b][k] * conj(H[k]) (conj_h = 1), elementwise, for batch rows of N
  *   points; Z may alias X.  scale multiplies the result (exact for powers of 2).
  * fft_filter_grad_h: grad_H[k] = sum_b conj(X[b][k]) * G[b][k], accumulated in
- *   FP32 with a fixed-order tree (bitwise reproducible).  Uses the plan-free
- *   scratch `work` of fft_filter_grad_h_workspace(N, batch) bytes.
- * fft_spectral_filter_fused: one kernel per row doing forward FFT, multiply
- *   by H (or conj H) and inverse FFT in shared memory (one HBM round trip);
- *   direction of the outer transform pair given by `adjoint` (0: y =
- *   IFFT(FFT(x) H); 1: y = FFT-adjoint pair used by the backward pass,
- *   g = (1/N) FFT(g_y) * conj(H) then F^H).  N in [256, 16384].
- * All pointers are device pointers, 16-byte aligned; asynchronous on stream.
+ *   FP32 in 32-row chunks and a fixed-order pairwise tree (bitwise
+ *   reproducible); `work` must hold fft_filter_grad_h_workspace(N, batch)
+ *   bytes.
+ * All pointers are device pointers, 16-byte aligned (8 for grad_h); all
+ * calls are asynchronous on stream.
  */
 fft_status_t fft_filter_apply(const void *X, const void *H, void *Z, int N,
                               int64_t batch, int conj_h, float scale, void *stream);
 int64_t fft_filter_grad_h_workspace(int N, int64_t batch);
 fft_status_t fft_filter_grad_h(const void *X, const void *G, void *grad_H, int N,
                                int64_t batch, void *work, void *stream);
-fft_status_t fft_spectral_filter_fused(const void *x, const void *H, void *y, int N,
-                                       int64_t batch, int adjoint, void *stream);
+
+/*
+ * Fused spectral filter: the forward FFT, the multiplication by H and the
+ * inverse FFT of a row run in ONE kernel with the row in registers (after a
+ * Stockham transform each thread already holds the points the next
+ * transform's first pass reads), so a row crosses HBM once each way.
+ *
+ * fft_filter_plan: plan for `batch` rows of N points, N power of two in
+ *   [256, 16384] (FFT_ERR_NOT_SUPPORTED otherwise).  Owns the twiddle tables
+ *   and the backward pass's per-CTA partial sums.  Free with fft_destroy.
+ * fft_filter_forward: y = IFFT(FFT(x) * H) (conj_h = 1: * conj(H)), inverse
+ *   scaled by 1/N; if X_save is non-NULL it also receives FFT(x) (needed by
+ *   the backward).  x, y, X_save: batch*N float2; H: N float2.
+ * fft_filter_backward: with g_y = dL/dy (PyTorch convention),
+ *   grad_x = IFFT(FFT(g_y) * conj(H)) = F^H(conj(H) * g_z), g_z = FFT(g_y)/N,
+ *   grad_H = sum_rows conj(X_saved) * g_z  (per-CTA partials + fixed-order
+ *   tree: bitwise reproducible on a given GPU).
+ * Device pointers, 16-byte aligned; asynchronous on stream.
+ */
+fft_status_t fft_filter_plan(fft_plan_t *out, int N, int64_t batch);
+fft_status_t fft_filter_forward(fft_plan_t plan, const void *x, const void *H, void *y,
+                                void *X_save, int conj_h, void *stream);
+fft_status_t fft_filter_backward(fft_plan_t plan, const void *g_y, const void *H,
+                                 const void *X_saved, void *grad_x, void *grad_H,
+                                 void *stream);
 
 /*
  * fft_fourstep_noalloc — the two-phase four-step transform (same kernels and

@@ -21,7 +21,8 @@ __all__ = [
     "fft_exec_host", "fft_destroy", "fft_plan_info", "fft_last_device_status",
     "fft_twiddle_table", "fft_twiddle_index", "fft_ragged_plan", "fft_autotune",
     "fft_autotune_load", "fft_autotune_clear", "fft_filter_apply",
-    "fft_filter_grad_h_workspace", "fft_filter_grad_h", "fft_spectral_filter_fused",
+    "fft_filter_grad_h_workspace", "fft_filter_grad_h", "fft_filter_plan",
+    "fft_filter_forward", "fft_filter_backward", "FFT_PATH_FILTER",
     "PlanInfo", "Config", "EXPORTED_SYMBOLS", "fft_list_configs", "fft_plan_config",
     "fft_fourstep_noalloc", "FFT_NOALLOC_MAX_POINTS",
 ]
@@ -35,6 +36,7 @@ FFT_FLAG_FORCE_FOURSTEP = 0x4
 FFT_FLAG_NO_AUTOTUNE_CACHE = 0x8
 FFT_FLAG_ADJOINT = 0x10
 FFT_PATH_SINGLE_CTA, FFT_PATH_FOURSTEP, FFT_PATH_RAGGED, FFT_PATH_TENSORCORE = 1, 2, 3, 4
+FFT_PATH_FILTER = 5
 FFT_NOALLOC_MAX_POINTS = 2097152
 
 STATUS = {
@@ -117,7 +119,9 @@ _SIGS = {
     "fft_filter_apply": ([_vp, _vp, _vp, _i32, _i64, _i32, _f32, _vp], _i32),
     "fft_filter_grad_h_workspace": ([_i32, _i64], _i64),
     "fft_filter_grad_h": ([_vp, _vp, _vp, _i32, _i64, _vp, _vp], _i32),
-    "fft_spectral_filter_fused": ([_vp, _vp, _vp, _i32, _i64, _i32, _vp], _i32),
+    "fft_filter_plan": ([ctypes.POINTER(_vp), _i32, _i64], _i32),
+    "fft_filter_forward": ([_vp, _vp, _vp, _vp, _vp, _i32, _vp], _i32),
+    "fft_filter_backward": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp], _i32),
     "fft_list_configs": ([_i32, _vp, _i32], _i32),
     "fft_plan_config": ([ctypes.POINTER(_vp), _i32, _i64, _i32, _i32, ctypes.POINTER(Config)], _i32),
     "fft_fourstep_noalloc": ([_vp, _vp, _i32, _i64, _i32, _vp], _i32),
@@ -276,11 +280,21 @@ def fft_filter_grad_h(X, G, grad_H, N: int, batch: int, work, stream=None) -> No
                                    _stream(stream)), "fft_filter_grad_h")
 
 
-def fft_spectral_filter_fused(x, H, y, N: int, batch: int, adjoint: bool = False,
-                              stream=None) -> None:
-    _check(lib().fft_spectral_filter_fused(_ptr(x), _ptr(H), _ptr(y), N, batch,
-                                           int(bool(adjoint)), _stream(stream)),
-           "fft_spectral_filter_fused")
+def fft_filter_plan(N: int, batch: int) -> int:
+    h = _vp()
+    _check(lib().fft_filter_plan(ctypes.byref(h), N, batch), "fft_filter_plan")
+    return h.value
+
+
+def fft_filter_forward(plan: int, x, H, y, X_save=None, conj_h: bool = False,
+                       stream=None) -> None:
+    _check(lib().fft_filter_forward(plan, _ptr(x), _ptr(H), _ptr(y), _ptr(X_save),
+                                    int(bool(conj_h)), _stream(stream)), "fft_filter_forward")
+
+
+def fft_filter_backward(plan: int, g_y, H, X_saved, grad_x, grad_H, stream=None) -> None:
+    _check(lib().fft_filter_backward(plan, _ptr(g_y), _ptr(H), _ptr(X_saved), _ptr(grad_x),
+                                     _ptr(grad_H), _stream(stream)), "fft_filter_backward")
 
 
 def fft_list_configs(N: int) -> list:

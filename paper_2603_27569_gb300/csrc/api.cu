@@ -361,6 +361,7 @@ static fft_status_t plan_single(fft_plan_impl *pl, const KernelEntry *k, int cta
 static void free_plan(fft_plan_impl *pl) {
   if (!pl) return;
   if (pl->ragged) ragged_destroy(pl);
+  if (pl->filter) filter_destroy(pl);
   if (pl->tc) tc_destroy(pl);
   if (pl->d_tw) cudaFree(pl->d_tw);
   if (pl->d_scratch) cudaFree(pl->d_scratch);
@@ -567,6 +568,7 @@ fft_status_t fft_exec(fft_plan_t plan, const void *in, void *out, void *stream) 
     if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return FFT_ERR_MISALIGNED;
     return ragged_exec(pl, (const float2 *)in, (float2 *)out, (cudaStream_t)stream);
   }
+  if (pl->path == FFT_PATH_FILTER) return FFT_ERR_INVALID_VALUE;  // use fft_filter_forward
   if (pl->batch == 0) return FFT_OK;
   fft_status_t s = check_buffers(in, out, (int64_t)sizeof(float2) * pl->N * pl->batch);
   if (s != FFT_OK) return s;
@@ -576,7 +578,7 @@ fft_status_t fft_exec(fft_plan_t plan, const void *in, void *out, void *stream) 
 fft_status_t fft_exec_host(fft_plan_t plan, const void *host_in, void *host_out, void *stream) {
   if (!plan) return FFT_ERR_INVALID_VALUE;
   fft_plan_impl *pl = &plan->impl;
-  if (pl->path == FFT_PATH_RAGGED) return FFT_ERR_NOT_SUPPORTED;
+  if (pl->path == FFT_PATH_RAGGED || pl->path == FFT_PATH_FILTER) return FFT_ERR_NOT_SUPPORTED;
   if (pl->batch == 0) return FFT_OK;
   if (!host_in || !host_out) return FFT_ERR_INVALID_VALUE;
   cudaStream_t st = (cudaStream_t)stream;

@@ -56,6 +56,8 @@ struct fft_plan_impl {
   void *tc = nullptr;
   // ragged path
   RaggedState *ragged = nullptr;
+  // fused spectral-filter path
+  void *filter = nullptr;
 };
 
 // Helpers implemented in api.cu, shared with the other units.
@@ -92,6 +94,9 @@ fft_status_t tc_plan(fft_plan_impl *pl);
 fft_status_t tc_exec(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t rows,
                      cudaStream_t st);
 void tc_destroy(fft_plan_impl *pl);
+
+// Fused spectral filter (filter_fused.cu)
+void filter_destroy(fft_plan_impl *pl);
 
 // Ragged path (ragged.cu)
 fft_status_t ragged_exec(fft_plan_impl *pl, const float2 *in, float2 *out, cudaStream_t st);

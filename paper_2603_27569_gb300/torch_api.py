@@ -213,17 +213,97 @@ class _SpectralFilterFn(torch.autograd.Function):
         return grad_x, grad_H
 
 
-def spectral_filter(x: torch.Tensor, H: torch.Tensor) -> torch.Tensor:
-    """y = IFFT(FFT(x) * H) along the last dimension; differentiable in x and H."""
+class _FilterPlan:
+    """Owns one fused spectral-filter plan (fft_filter_plan)."""
+
+    def __init__(self, N: int, batch: int, device):
+        self.device = torch.device(device)
+        with torch.cuda.device(self.device):
+            self.handle = B.fft_filter_plan(N, batch)
+
+    def close(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h:
+            try:
+                with torch.cuda.device(self.device):
+                    B.fft_destroy(h)
+            except Exception:
+                pass
+
+    def __del__(self):
+        self.close()
+
+
+_fcache: "collections.OrderedDict[tuple, _FilterPlan]" = collections.OrderedDict()
+
+
+def _filter_plan(N: int, batch: int, device) -> _FilterPlan:
+    key = (torch.device(device).index, N, batch)
+    with _cache_lock:
+        p = _fcache.get(key)
+        if p is not None:
+            _fcache.move_to_end(key)
+            return p
+    p = _FilterPlan(N, batch, device)
+    with _cache_lock:
+        _fcache[key] = p
+        while len(_fcache) > _CACHE_MAX:
+            _fcache.popitem(last=False)
+    return p
+
+
+class _FusedSpectralFilterFn(torch.autograd.Function):
+    """Forward FFT, * H and inverse FFT in one kernel per row (and the backward
+    likewise): each row crosses HBM once each way."""
+
+    @staticmethod
+    def forward(ctx, x, H):
+        N = x.shape[-1]
+        batch = x.numel() // N
+        xc = x.contiguous()
+        Hc = H.contiguous()
+        plan = _filter_plan(N, batch, x.device)
+        y = torch.empty_like(xc)
+        need_grad = ctx.needs_input_grad[0] or ctx.needs_input_grad[1]
+        X = torch.empty_like(xc) if need_grad else None
+        B.fft_filter_forward(plan.handle, xc, Hc, y, X, False,
+                             torch.cuda.current_stream(x.device))
+        ctx.save_for_backward(X if X is not None else xc, Hc)
+        ctx.shape = x.shape
+        return y.view(x.shape)
+
+    @staticmethod
+    def backward(ctx, gy):
+        X, H = ctx.saved_tensors
+        N = X.shape[-1]
+        batch = X.numel() // N
+        plan = _filter_plan(N, batch, X.device)
+        gx = torch.empty_like(X)
+        gH = torch.empty(N, dtype=torch.complex64, device=X.device)
+        B.fft_filter_backward(plan.handle, gy.contiguous(), H, X, gx, gH,
+                              torch.cuda.current_stream(X.device))
+        return (gx.view(ctx.shape) if ctx.needs_input_grad[0] else None,
+                gH if ctx.needs_input_grad[1] else None)
+
+
+def spectral_filter(x: torch.Tensor, H: torch.Tensor, fused: bool = True) -> torch.Tensor:
+    """y = IFFT(FFT(x) * H) along the last dimension; differentiable in x and H.
+
+    fused=True runs forward FFT, multiply and inverse FFT in one kernel per row
+    (N = 256..16384); fused=False runs them as separate library kernels."""
+    N = x.shape[-1]
+    if fused and 256 <= N <= 16384:
+        return _FusedSpectralFilterFn.apply(x, H)
     return _SpectralFilterFn.apply(x, H)
 
 
 class SpectralFilter(torch.nn.Module):
     """Learnable matched filter H (complex64 [N]) applied in the frequency domain."""
 
-    def __init__(self, H: torch.Tensor):
+    def __init__(self, H: torch.Tensor, fused: bool = True):
         super().__init__()
         self.H = torch.nn.Parameter(H.detach().clone().to(torch.complex64))
+        self.fused = fused
 
     def forward(self, x: torch.Tensor) -> torch.Tensor:
-        return spectral_filter(x, self.H)
+        return spectral_filter(x, self.H, self.fused)

@@ -33,21 +33,23 @@ def sar_case(rows, N, Np, seed=0):
     return x, H, m
 
 
-def gpu_filter_grads(x, H, m):
+def gpu_filter_grads(x, H, m, fused=True):
     xd = to_dev(x).requires_grad_(True)
-    layer = fg.SpectralFilter(to_dev(H))
+    layer = fg.SpectralFilter(to_dev(H), fused=fused)
     y = layer(xd)
     md = to_dev(m)
     loss = (md * (y.real ** 2 + y.imag ** 2)).sum()
     loss.backward()
     torch.cuda.synchronize()
-    return to_host(y), to_host(xd.grad), to_host(layer.H.grad), float(loss)
+    return to_host(y), to_host(xd.grad), to_host(layer.H.grad), float(loss.detach())
 
 
-@pytest.mark.parametrize("rows,N,Np", [(4, 256, 64), (64, 8192, 2048), (3, 16384, 4096)])
-def test_spectral_filter_forward_and_grads_match_oracle(rows, N, Np):
+@pytest.mark.parametrize("fused", [True, False])
+@pytest.mark.parametrize("rows,N,Np", [(4, 256, 64), (37, 1024, 256), (64, 8192, 2048),
+                                       (3, 16384, 4096)])
+def test_spectral_filter_forward_and_grads_match_oracle(rows, N, Np, fused):
     x, H, m = sar_case(rows, N, Np)
-    y, gx, gH, loss = gpu_filter_grads(x, H, m)
+    y, gx, gH, loss = gpu_filter_grads(x, H, m, fused=fused)
     want_y = oracle.spectral_filter_forward(x, H)
     assert rel_l2_rows(y, want_y).max() <= 2 * TOL_FP32
     ogx, ogH = oracle.spectral_filter_grads(x, H, m)
@@ -56,11 +58,32 @@ def test_spectral_filter_forward_and_grads_match_oracle(rows, N, Np):
     assert abs(loss - oracle.spectral_filter_loss(x, H, m)) <= 1e-5 * abs(loss)
 
 
-def test_spectral_filter_grad_h_is_bitwise_reproducible():
+@pytest.mark.parametrize("fused", [True, False])
+def test_spectral_filter_grad_h_is_bitwise_reproducible(fused):
     x, H, m = sar_case(100, 1024, 256, seed=4)
-    _, _, g1, _ = gpu_filter_grads(x, H, m)
-    _, _, g2, _ = gpu_filter_grads(x, H, m)
+    _, _, g1, _ = gpu_filter_grads(x, H, m, fused)
+    _, _, g2, _ = gpu_filter_grads(x, H, m, fused)
     assert np.array_equal(g1.view(np.uint32), g2.view(np.uint32))
+
+
+@pytest.mark.parametrize("N", [256, 512, 2048, 4096, 8192, 16384])
+def test_fused_filter_abi_conj_and_saved_spectrum(N):
+    # through the C ABI: conj_h, the saved spectrum, and an odd row count
+    rows = 7
+    x = synth.gaussian((rows, N), seed=N)
+    H = synth.gaussian(N, seed=N + 1)
+    plan = fg.fft_filter_plan(N, rows)
+    xd, Hd = to_dev(x), to_dev(H)
+    y = torch.empty_like(xd)
+    X = torch.empty_like(xd)
+    st = torch.cuda.current_stream()
+    fg.fft_filter_forward(plan, xd, Hd, y, X, True, st)
+    torch.cuda.synchronize()
+    fg.fft_destroy(plan)
+    want_X = oracle.fft(x)
+    want_y = oracle.ifft(want_X * np.conj(H.astype(np.complex128)))
+    assert rel_l2_rows(to_host(X), want_X).max() <= TOL_FP32
+    assert rel_l2_rows(to_host(y), want_y).max() <= 2 * TOL_FP32
 
 
 @pytest.mark.parametrize("N", [256, 16384])
