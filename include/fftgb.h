@@ -96,6 +96,7 @@ typedef struct {
     int twiddle_mode;       /* as in fft_config_t                              */
     int grid_ctas;          /* CTAs launched per exec (0 = one per tile)      */
     int tma_slabs;          /* as in fft_config_t                              */
+    int cluster_split;      /* as in fft_config_t                              */
 } fft_plan_info_t;
 
 /* One compiled execution configuration (see fft_list_configs). */
@@ -115,6 +116,9 @@ typedef struct {
     int tma_slabs;          /* > 0: TMA-staged persistent kernel keeping this many
                                slabs of the next row in a shared-memory ring;
                                0: pass 0 loads straight from global memory      */
+    int cluster_split;      /* 2: each row on a 2-CTA thread-block cluster (halves
+                               of N/2 points combined through distributed shared
+                               memory); 0: one CTA per row                      */
 } fft_config_t;
 
 /* Human-readable name of a status code (static string, never NULL). */

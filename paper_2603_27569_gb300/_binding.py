@@ -65,6 +65,7 @@ class PlanInfo(ctypes.Structure):
         ("radix", ctypes.c_int * 8), ("n1", ctypes.c_int), ("n2", ctypes.c_int),
         ("scratch_bytes", ctypes.c_int64), ("twiddle_mode", ctypes.c_int),
         ("grid_ctas", ctypes.c_int), ("tma_slabs", ctypes.c_int),
+        ("cluster_split", ctypes.c_int),
     ]
 
     def as_dict(self) -> dict:
@@ -79,7 +80,7 @@ class Config(ctypes.Structure):
         ("transforms_per_cta", ctypes.c_int), ("threads_per_cta", ctypes.c_int),
         ("num_passes", ctypes.c_int), ("radix", ctypes.c_int * 8), ("n1", ctypes.c_int),
         ("twiddle_mode", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
-        ("tma_slabs", ctypes.c_int),
+        ("tma_slabs", ctypes.c_int), ("cluster_split", ctypes.c_int),
     ]
 
     def as_dict(self) -> dict:

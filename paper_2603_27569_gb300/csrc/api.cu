@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "column.cuh"
+#include "cluster.cuh"
 #include "staged.cuh"
 #include "plan.h"
 
@@ -62,10 +63,21 @@ const KernelEntry *find_staged(int N, int P, int C, const int *radix, int npass,
   return nullptr;
 }
 
+const KernelEntry *find_kind(int kind, int N, int P, const int *radix, int npass, int twm) {
+  for (const auto &e : kernel_registry()) {
+    if (e.kind != kind || e.N != N || e.P != P || e.npass != npass || e.twm != twm) continue;
+    bool same = true;
+    for (int i = 0; i < npass; ++i) same = same && e.radix[i] == radix[i];
+    if (same) return &e;
+  }
+  return nullptr;
+}
+
 const KernelEntry *default_stockham(int N) {
   const KernelEntry *any = nullptr;
   for (const auto &e : kernel_registry()) {
-    if ((e.kind != KIND_STOCKHAM && e.kind != KIND_STAGED) || e.N != N) continue;
+    if ((e.kind != KIND_STOCKHAM && e.kind != KIND_STAGED && e.kind != KIND_SPLIT2) || e.N != N)
+      continue;
     if (e.is_default) return &e;
     if (!any && e.kind == KIND_STOCKHAM) any = &e;
   }
@@ -216,6 +228,25 @@ static fft_status_t launch_staged(const KernelEntry *k, int dir, const float2 *i
   return FFT_OK;
 }
 
+static fft_status_t launch_split2(const KernelEntry *k, int dir, const float2 *in, float2 *out,
+                                  const float2 *tw, const float2 *tw_n, int64_t rows,
+                                  float scale, cudaStream_t st) {
+  if (rows <= 0) return FFT_OK;
+  Split2Args a;
+  a.in = in;
+  a.out = out;
+  a.tw = tw;
+  a.tw_n = tw_n;
+  a.batch = rows;
+  a.scale = scale;
+  const int64_t grid = 2 * rows;
+  if (grid > 0x7fffffffLL) return FFT_ERR_INVALID_SIZE;
+  void *args[] = {&a};
+  FFTGB_CUDA(cudaLaunchKernel(k->fn[dir > 0 ? 1 : 0], dim3((unsigned)grid), dim3(k->threads),
+                              args, k->smem, st));
+  return FFT_OK;
+}
+
 static fft_status_t launch_column(const KernelEntry *k, int dir, const ColumnArgs &ca,
                                   cudaStream_t st) {
   const int64_t grid = ca.nmat * (ca.ncols / k->TB);
@@ -231,6 +262,10 @@ static fft_status_t launch_column(const KernelEntry *k, int dir, const ColumnArg
 fft_status_t exec_rows(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t rows,
                        cudaStream_t st) {
   if (rows <= 0) return FFT_OK;
+  if (pl->path == FFT_PATH_SINGLE_CTA && pl->k_single->kind == KIND_SPLIT2) {
+    return launch_split2(pl->k_single, pl->direction, in, out, pl->d_tw + pl->tw_single,
+                         pl->d_tw + pl->tw_big, rows, pl->scale, st);
+  }
   if (pl->path == FFT_PATH_SINGLE_CTA && pl->k_single->kind == KIND_STAGED) {
     return launch_staged(pl->k_single, pl->direction, in, out, pl->d_tw + pl->tw_single, rows,
                          pl->scale, pl->grid_ctas, pl->d_status, st);
@@ -350,11 +385,22 @@ static fft_status_t plan_single(fft_plan_impl *pl, const KernelEntry *k, int cta
   fft_status_t s = ensure_smem_attr(k);
   if (s != FFT_OK) return s;
   if (k->kind == KIND_STAGED) ctas_per_sm = 1;  // one resident CTA per SM by design
+  if (k->kind == KIND_SPLIT2) ctas_per_sm = 0;  // one cluster per row
   pl->ctas_per_sm = ctas_per_sm;
   pl->grid_ctas = ctas_per_sm != 0 ? persistent_grid(k, ctas_per_sm) : 0;
   int64_t off = 0;
   pl->tw_single = 0;
   auto segs = pass_segments(*k, off);
+  if (k->kind == KIND_SPLIT2) {  // + W_N^k for the cluster combine
+    TwSeg g;
+    g.offset = off;
+    g.count = pl->N;
+    g.kind = 1;
+    g.p = g.r = 0;
+    g.M = pl->N;
+    pl->tw_big = off;
+    segs.push_back(g);
+  }
   return build_twiddles(pl, segs);
 }
 
@@ -436,7 +482,10 @@ static fft_status_t plan_common(fft_plan_t *out, int N, int64_t batch, int direc
         s = plan_fourstep(pl, cfg->n1);
       } else if (cfg->path == FFT_PATH_SINGLE_CTA) {
         const KernelEntry *k =
-            cfg->tma_slabs > 0
+            cfg->cluster_split == 2
+                ? find_kind(KIND_SPLIT2, N, cfg->points_per_thread, cfg->radix, cfg->num_passes,
+                            cfg->twiddle_mode)
+            : cfg->tma_slabs > 0
                 ? find_staged(N, cfg->points_per_thread, cfg->tma_slabs, cfg->radix,
                               cfg->num_passes, cfg->twiddle_mode)
                 : find_stockham(N, cfg->points_per_thread, cfg->transforms_per_cta, cfg->radix,
@@ -459,9 +508,10 @@ static fft_status_t plan_common(fft_plan_t *out, int N, int64_t batch, int direc
         s = plan_fourstep(pl, tc.n1);
         if (s == FFT_ERR_NOT_SUPPORTED) have = false;
       } else if (have) {
-        const KernelEntry *k = tc.slabs > 0
-                                   ? find_staged(N, tc.P, tc.slabs, tc.radix, tc.npass, tc.twm)
-                                   : find_stockham(N, tc.P, tc.TB, tc.radix, tc.npass, tc.twm);
+        const KernelEntry *k =
+            tc.split == 2  ? find_kind(KIND_SPLIT2, N, tc.P, tc.radix, tc.npass, tc.twm)
+            : tc.slabs > 0 ? find_staged(N, tc.P, tc.slabs, tc.radix, tc.npass, tc.twm)
+                           : find_stockham(N, tc.P, tc.TB, tc.radix, tc.npass, tc.twm);
         if (k) s = plan_single(pl, k, tc.ctas_per_sm);
         else have = false;
       }
@@ -516,6 +566,20 @@ int fft_list_configs(int N, fft_config_t *out, int capacity) {
       c.ctas_per_sm = shape;
       emit(c);
     }
+  }
+  for (const auto &e : kernel_registry()) {
+    if (e.kind != KIND_SPLIT2 || e.N != N) continue;
+    fft_config_t c;
+    memset(&c, 0, sizeof(c));
+    c.path = FFT_PATH_SINGLE_CTA;
+    c.points_per_thread = e.P;
+    c.transforms_per_cta = 1;
+    c.threads_per_cta = e.threads;
+    c.num_passes = e.npass;
+    for (int i = 0; i < 8; ++i) c.radix[i] = e.radix[i];
+    c.twiddle_mode = e.twm;
+    c.cluster_split = 2;
+    emit(c);
   }
   for (const auto &e : kernel_registry()) {
     if (e.kind != KIND_STAGED || e.N != N) continue;
@@ -678,6 +742,8 @@ fft_status_t fft_plan_info(fft_plan_t plan, fft_plan_info_t *info) {
   info->twiddle_mode = pl->path == FFT_PATH_SINGLE_CTA ? pl->k_single->twm : 0;
   info->grid_ctas = (int)pl->grid_ctas;
   info->tma_slabs = pl->path == FFT_PATH_SINGLE_CTA ? pl->k_single->slabs : 0;
+  info->cluster_split =
+      (pl->path == FFT_PATH_SINGLE_CTA && pl->k_single->kind == KIND_SPLIT2) ? 2 : 0;
   return FFT_OK;
 }
 

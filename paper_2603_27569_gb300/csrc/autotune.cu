@@ -67,9 +67,9 @@ fft_status_t write_json(const char *path) {
     const auto &c = kv.second.choice;
     fprintf(f, "%s  {\"N\": %d, \"direction\": %d, \"precision\": %d, \"path\": %d, \"P\": %d, "
                "\"TB\": %d, \"n1\": %d, \"twm\": %d, \"ctas_per_sm\": %d, \"slabs\": %d, "
-               "\"radix\": [",
+               "\"split\": %d, \"radix\": [",
             first ? "" : ",\n", kv.first.N, kv.first.dir, kv.first.prec, c.path, c.P, c.TB, c.n1,
-            c.twm, c.ctas_per_sm, c.slabs);
+            c.twm, c.ctas_per_sm, c.slabs, c.split);
     for (int i = 0; i < c.npass; ++i) fprintf(f, "%s%d", i ? ", " : "", c.radix[i]);
     fprintf(f, "], \"us\": %.3f, \"batch\": %lld}", kv.second.us, (long long)kv.second.batch);
     first = false;
@@ -115,7 +115,8 @@ fft_status_t load_json(const char *path) {
               read_int(s, "TB", b, e, &en.choice.TB) && read_int(s, "n1", b, e, &en.choice.n1) &&
               read_int(s, "twm", b, e, &en.choice.twm) &&
               read_int(s, "ctas_per_sm", b, e, &en.choice.ctas_per_sm) &&
-              read_int(s, "slabs", b, e, &en.choice.slabs);
+              read_int(s, "slabs", b, e, &en.choice.slabs) &&
+              read_int(s, "split", b, e, &en.choice.split);
     size_t r = s.find("\"radix\": [", b);
     if (ok && r != std::string::npos && r < e) {
       const char *q = s.c_str() + r + 10;
@@ -214,6 +215,7 @@ fft_status_t fft_autotune(int N, int direction, int precision, int64_t batch,
       best.twm = c.twiddle_mode;
       best.ctas_per_sm = c.ctas_per_sm;
       best.slabs = c.tma_slabs;
+      best.split = c.cluster_split;
     }
   }
   cudaEventDestroy(e0);

@@ -1,5 +1,6 @@
 // Helpers that instantiate a kernel configuration and register it.
 #pragma once
+#include "cluster.cuh"
 #include "column.cuh"
 #include "registry.h"
 #include "staged.cuh"
@@ -51,6 +52,23 @@ inline KernelEntry staged_entry() {
   return e;
 }
 
+template <int N, int P, int TWM, int DEF, class SC>
+inline KernelEntry split2_entry() {
+  KernelEntry e{};
+  e.kind = KIND_SPLIT2;
+  e.N = N;
+  e.P = P;
+  e.TB = 1;
+  e.threads = (N / 2) / P;
+  e.smem = sizeof(float2) * (size_t)(N / 2);
+  fill_radix<SC>(e);
+  e.is_default = DEF;
+  e.twm = TWM;
+  e.fn[0] = (const void *)&split2_kernel<N, P, -1, SC, TWM>;
+  e.fn[1] = (const void *)&split2_kernel<N, P, +1, SC, TWM>;
+  return e;
+}
+
 template <int L, int P, int C, int VAR, int DEF, class SC>
 inline KernelEntry column_entry() {
   KernelEntry e{};
@@ -87,6 +105,13 @@ inline KernelEntry column_entry() {
       ::fftgb::staged_entry<N, P, C, 0, DEF == 1, ::fftgb::Sched<__VA_ARGS__>>()); \
   static ::fftgb::Registrar FFTGB_CAT(fftgb_reg_, __COUNTER__)(              \
       ::fftgb::staged_entry<N, P, C, 1, DEF == 2, ::fftgb::Sched<__VA_ARGS__>>())
+// FFTGB_SPLIT2(N, P, is_default, radices of N/2...): cluster-split kernel,
+// both twiddle modes (is_default as for FFTGB_STOCKHAM).
+#define FFTGB_SPLIT2(N, P, DEF, ...)                                         \
+  static ::fftgb::Registrar FFTGB_CAT(fftgb_reg_, __COUNTER__)(              \
+      ::fftgb::split2_entry<N, P, 0, DEF == 1, ::fftgb::Sched<__VA_ARGS__>>()); \
+  static ::fftgb::Registrar FFTGB_CAT(fftgb_reg_, __COUNTER__)(              \
+      ::fftgb::split2_entry<N, P, 1, DEF == 2, ::fftgb::Sched<__VA_ARGS__>>())
 // FFTGB_COLUMN(L, P, C, variant, is_default, radices...)
 #define FFTGB_COLUMN(L, P, C, VAR, DEF, ...)                                 \
   static ::fftgb::Registrar FFTGB_CAT(fftgb_reg_, __COUNTER__)(              \

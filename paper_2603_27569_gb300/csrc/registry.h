@@ -8,17 +8,17 @@
 
 namespace fftgb {
 
-enum KernelKind { KIND_STOCKHAM = 1, KIND_COLUMN = 2, KIND_STAGED = 3 };
+enum KernelKind { KIND_STOCKHAM = 1, KIND_COLUMN = 2, KIND_STAGED = 3, KIND_SPLIT2 = 4 };
 
 struct KernelEntry {
   int kind;
-  int N;          // transform length (L for column kernels)
+  int N;          // transform length (L for column kernels; the full N for split2)
   int P;          // complex points per thread
   int TB;         // rows per CTA (single-CTA) / columns per CTA (column)
   int threads;    // threads per CTA
   size_t smem;    // dynamic shared memory bytes
   int npass;
-  int radix[8];
+  int radix[8];   // (split2: the schedule of the N/2-point half)
   int tw_total;   // entries of the per-pass twiddle tables
   int is_default; // the built-in choice for this (kind, N, variant)
   int variant;    // column kernels: 0 plain, 1 twiddle + transposed store

@@ -102,7 +102,11 @@ def test_configs_listed_for_every_supported_size(L):
             prod = 1
             for r in c["radix"]:
                 prod *= r
-            if c["path"] == fg.FFT_PATH_SINGLE_CTA:
+            if c["path"] == fg.FFT_PATH_SINGLE_CTA and c["cluster_split"] == 2:
+                # each CTA of the pair transforms N/2 points
+                assert prod == N // 2
+                assert c["threads_per_cta"] == (N // 2) // c["points_per_thread"]
+            elif c["path"] == fg.FFT_PATH_SINGLE_CTA:
                 assert prod == N
                 assert all(c["points_per_thread"] % r == 0 for r in c["radix"])
                 assert c["threads_per_cta"] == c["transforms_per_cta"] * N // c["points_per_thread"]
