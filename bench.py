@@ -228,7 +228,7 @@ def run_ours(args):
 
     import paper_2603_27569_gb300 as fg
     from paper_2603_27569_gb300 import build as fbuild
-    from paper_2603_27569_gb300 import synth
+    from paper_2603_27569_gb300 import shard, synth
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -294,11 +294,7 @@ def run_ours(args):
         torch.distributed.barrier()
     time.sleep(0.3)
     clocks.stop()
-    total_ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = shard.max_over_ranks(t_start.elapsed_time(t_end))
     ms_per_step = total_ms / args.steps
     step_flops = sum(flops(N, POINTS // N) for (N, _d) in keys)
     value = step_flops * args.steps * world / (total_ms * 1e-3) / 1e9
@@ -354,11 +350,7 @@ def run_ours(args):
             for k in keys:
                 plans[k].exec_host(xh, yh)
         torch.cuda.synchronize()
-        e_s = time.perf_counter() - t0
-        if world > 1:
-            tt = torch.tensor([e_s], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            e_s = float(tt.item())
+        e_s = shard.max_over_ranks(time.perf_counter() - t0)
         e2e = {"value": round(step_flops * e_steps * world / e_s / 1e9, 2), "unit": "GFLOPS",
                "h2d_bytes_per_step": 8 * POINTS * len(keys),
                "d2h_bytes_per_step": 8 * POINTS * len(keys),
