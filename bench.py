@@ -541,19 +541,53 @@ def run_profile_case(args):
 
     import paper_2603_27569_gb300 as fg
     from paper_2603_27569_gb300 import build as fbuild
+    from paper_2603_27569_gb300 import synth
 
     fbuild.build()
     N = args.profile_case
     batch = POINTS // N            # 256 MiB in: larger than L2
+    kind = args.profile_kind
     x = torch.randn(batch * N, dtype=torch.complex64, device="cuda")
     y = torch.empty_like(x)
-    cfg = json.loads(args.profile_config) if args.profile_config else None
-    p = fg.Plan(N, batch, fg.FFT_FORWARD, flags=args.profile_flags, config=cfg)
-    for _ in range(3):
-        p(x, out=y)
+    st = torch.cuda.current_stream()
+    if kind == "plan":
+        cfg = json.loads(args.profile_config) if args.profile_config else None
+        p = fg.Plan(N, batch, fg.FFT_FORWARD, flags=args.profile_flags, config=cfg)
+        for _ in range(3):
+            p(x, out=y)
+        info = p.info()
+        p.close()
+    elif kind == "tc":
+        p = fg.Plan(N, batch, fg.FFT_FORWARD, precision=fg.FFT_PREC_FP16X2)
+        for _ in range(3):
+            p(x, out=y)
+        info = p.info()
+        p.close()
+    elif kind in ("filter_fwd", "filter_bwd"):
+        H = torch.randn(N, dtype=torch.complex64, device="cuda")
+        X = torch.empty_like(x)
+        h = fg.fft_filter_plan(N, batch)
+        gH = torch.empty_like(H)
+        for _ in range(3):
+            if kind == "filter_fwd":
+                fg.fft_filter_forward(h, x, H, y, X, False, st)
+            else:
+                fg.fft_filter_backward(h, x, H, X, y, gH, st)
+        info = fg.fft_plan_info(h)
+        fg.fft_destroy(h)
+    elif kind == "ragged":
+        d = synth.ragged_draw(20000, seed=0)
+        xr = torch.from_numpy(synth.gaussian(d["total"], seed=0)).cuda()
+        yr = torch.empty_like(xr)
+        h = fg.fft_ragged_plan(d["N"], d["direction"], d["offset"], d["offset"])
+        for _ in range(3):
+            fg.fft_exec(h, xr, yr, st)
+        info = fg.fft_plan_info(h)
+        fg.fft_destroy(h)
+    else:
+        raise SystemExit(f"unknown --profile-kind {kind}")
     torch.cuda.synchronize()
-    print("profile case ok", N, p.info(), flush=True)
-    p.close()
+    print("profile case ok", kind, N, info, flush=True)
     return 0
 
 
@@ -574,6 +608,8 @@ def main():
     ap.add_argument("--profile-case", type=int, default=0,
                     help="run one N of the sweep three times (for ncu) and exit")
     ap.add_argument("--profile-flags", type=int, default=0)
+    ap.add_argument("--profile-kind", default="plan",
+                    choices=["plan", "tc", "filter_fwd", "filter_bwd", "ragged"])
     ap.add_argument("--profile-config", type=str, default="",
                     help="JSON of one fft_list_configs entry to force")
     args = ap.parse_args()

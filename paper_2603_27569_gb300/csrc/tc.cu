@@ -123,6 +123,36 @@ __device__ __forceinline__ void tc_dft16(float2 (&x)[2][4], const uint32_t *__re
 
 __device__ __forceinline__ int tc_point(int t, int c) { return 2 * t + (c & 1) + (c >> 1) * 8; }
 
+// Shared-memory layout of the exchange after TC stage e: bit b (b < 4) of a
+// position is XOR-ed with bit src[e][b] (>= 4, or none), a permutation within
+// each 16-point block.  The source bits were chosen (by exhaustive search on a
+// model of the lane -> (butterfly, point) map) so that the half-warp accesses
+// of the writing stage and of the reading stage (TC gather or radix-4 tail)
+// hit at most 2 accesses per bank pair; the direct layout gives 4.
+__host__ __device__ constexpr int tc_src(int N, int e, int b) {
+  // rows: exchange e; columns: target bit b = 0..3
+  return N == 256     ? (e == 0 ? (b == 0 ? 4 : b == 1 ? -1 : b == 2 ? 6 : 5) : -1)
+         : N == 4096  ? (e == 0   ? (b == 0 ? 4 : b == 1 ? -1 : b == 2 ? 9 : 5)
+                         : e == 1 ? (b == 2 ? 5 : b == 3 ? 9 : -1)
+                                  : -1)
+         : N == 16384 ? (e == 0   ? (b == 0 ? 4 : b == 1 ? -1 : b == 2 ? 11 : 5)
+                         : e == 1 ? (b == 2 ? 5 : b == 3 ? 11 : -1)
+                         : e == 2 ? (b == 2 ? 9 : b == 3 ? 10 : -1)
+                                  : -1)
+                      : -1;
+}
+
+template <int N>
+__device__ __forceinline__ int tc_swz(int pos, int e) {
+  int a = 0;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int sb = tc_src(N, e, b);
+    if (sb >= 0) a |= ((pos >> sb) & 1) << b;
+  }
+  return pos ^ a;
+}
+
 // N = 16^S (S TC stages) or 16^S * 4 (radix-4 tail).  WPR warps per row, TB
 // rows per CTA, G groups of 16 butterflies per warp per stage.
 template <int N, int D, int PREC, int S, int TAIL, int WPR, int TB, int G>
@@ -158,7 +188,7 @@ tc_kernel(TcArgs a) {
         for (int c = 0; c < 4; ++c) {
           const int idx = i0 + g + 8 * r + tc_point(t, c) * NB;
           if (s == 0) x[q][r][c] = active ? __ldcs(src + idx) : make_float2(0.f, 0.f);
-          else x[q][r][c] = buf[idx];
+          else x[q][r][c] = buf[tc_swz<N>(idx, s - 1)];
         }
     }
     if (s > 0) __syncthreads();  // every read of the buffer is done
@@ -188,7 +218,7 @@ tc_kernel(TcArgs a) {
           if (last) {
             if (active) __stcs(a.out + row * N + pos, cscale(x[q][r][c], a.scale));
           } else {
-            buf[pos] = x[q][r][c];
+            buf[tc_swz<N>(pos, s)] = x[q][r][c];
           }
         }
       }
@@ -204,7 +234,7 @@ tc_kernel(TcArgs a) {
 #pragma unroll
     for (int q = 0; q < Q; ++q)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) v[q][j] = buf[rt + q * RT + j * (N / 4)];
+      for (int j = 0; j < 4; ++j) v[q][j] = buf[tc_swz<N>(rt + q * RT + j * (N / 4), S - 1)];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const int k = rt + q * RT;  // i = k since i < p

@@ -286,12 +286,21 @@ class _FusedSpectralFilterFn(torch.autograd.Function):
                 gH if ctx.needs_input_grad[1] else None)
 
 
-def spectral_filter(x: torch.Tensor, H: torch.Tensor, fused: bool = True) -> torch.Tensor:
+# Largest N at which the fused kernels measured faster than the separate ones
+# on GB300: a fused row does two transforms of compute for one HBM round trip,
+# and above 4096 points the transforms themselves are SM-bound.
+FUSED_MAX_N = 4096
+
+
+def spectral_filter(x: torch.Tensor, H: torch.Tensor, fused: bool | None = None) -> torch.Tensor:
     """y = IFFT(FFT(x) * H) along the last dimension; differentiable in x and H.
 
     fused=True runs forward FFT, multiply and inverse FFT in one kernel per row
-    (N = 256..16384); fused=False runs them as separate library kernels."""
+    (N = 256..16384); fused=False runs them as separate library kernels;
+    None picks the faster for N (fused up to FUSED_MAX_N)."""
     N = x.shape[-1]
+    if fused is None:
+        fused = N <= FUSED_MAX_N
     if fused and 256 <= N <= 16384:
         return _FusedSpectralFilterFn.apply(x, H)
     return _SpectralFilterFn.apply(x, H)
@@ -300,7 +309,7 @@ def spectral_filter(x: torch.Tensor, H: torch.Tensor, fused: bool = True) -> tor
 class SpectralFilter(torch.nn.Module):
     """Learnable matched filter H (complex64 [N]) applied in the frequency domain."""
 
-    def __init__(self, H: torch.Tensor, fused: bool = True):
+    def __init__(self, H: torch.Tensor, fused: bool | None = None):
         super().__init__()
         self.H = torch.nn.Parameter(H.detach().clone().to(torch.complex64))
         self.fused = fused
