@@ -361,6 +361,7 @@ def run_ours(args):
         extras["fwd_bwd"] = bench_fwd_bwd(fg, synth, torch, dev, per_key_ms)
         extras["ragged"] = bench_ragged(fg, synth, torch, dev)
         extras["tensorcore"] = bench_tc(fg, synth, torch, dev)
+        extras["fp16_storage"] = bench_fp16_storage(fg, torch, dev, per_key_ms)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nthreads = os.cpu_count() or 1
@@ -488,6 +489,34 @@ def bench_tc(fg, synth, torch, dev):
         res["fp16x2_speedup_vs_fp32"] = round(res["fp32"]["ms"] / res["fp16x2"]["ms"], 3)
         out[str(N)] = res
         del x, y, ref
+    return out
+
+
+def bench_fp16_storage(fg, torch, dev, per_key_ms):
+    """FP16-storage transforms (4 bytes per point in HBM, FP32 arithmetic) over
+    the sweep's sizes, 2^25 points per call, forward; vs the FP32 plan."""
+    out = {}
+    x = torch.randn(POINTS, dtype=torch.complex64, device=dev).to(torch.complex32)
+    y = torch.empty_like(x)
+    for N in SIZES:
+        p = fg.Plan(N, POINTS // N, fg.FFT_FORWARD, precision=fg.FFT_PREC_FP16_STORAGE,
+                    device=dev)
+        for _ in range(3):
+            p(x, out=y)
+        torch.cuda.synchronize()
+        reps = 10
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            p(x, out=y)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        p.close()
+        out[str(N)] = {"us": round(ms * 1e3, 2),
+                       "gflops": round(flops(N, POINTS // N) / (ms * 1e-3) / 1e9, 1),
+                       "frac_hbm": round(8.0 * POINTS / (ms * 1e-3) / 1e9 / peaks()[0], 4),
+                       "speedup_vs_fp32": round(per_key_ms[(N, fg.FFT_FORWARD)] / ms, 3)}
     return out
 
 

@@ -47,7 +47,11 @@ typedef enum { FFT_FORWARD = -1, FFT_INVERSE = 1 } fft_direction_t;
 typedef enum {
     FFT_PREC_FP32 = 0,    /* FP32 data and arithmetic (the plain path)        */
     FFT_PREC_FP16X2 = 1,  /* tensor-core radix-16 DFT, FP16 hi+lo operands     */
-    FFT_PREC_BF16X2 = 2   /* tensor-core radix-16 DFT, BF16 hi+lo operands     */
+    FFT_PREC_BF16X2 = 2,  /* tensor-core radix-16 DFT, BF16 hi+lo operands     */
+    FFT_PREC_FP16_STORAGE = 3 /* data in HBM as FP16 (re, im) pairs, 4 bytes per
+                               point; FP32 arithmetic; output rounded to FP16
+                               (overflow to infinity: the caller keeps
+                               |X| below 65504).  N in [256, 16384].          */
 } fft_precision_t;
 
 typedef enum {
@@ -126,7 +130,9 @@ const char *fft_status_string(fft_status_t status);
 
 /*
  * fft_plan — plan `batch` transforms of length N in one direction.
- * N: power of two, 2 <= N <= 16384.  batch >= 0 (0 makes a valid plan whose
+ * N: power of two, 2 <= N <= 65536.  Up to 16384 a row fits one CTA; above
+ * that only the two-phase four-step runs (N = n1 * n2, n1, n2 <= 256; its
+ * intermediate doubles the HBM traffic).  batch >= 0 (0 makes a valid plan whose
  * exec does nothing).  direction: FFT_FORWARD or FFT_INVERSE.
  * Allocates and fills the plan's twiddle tables on the current device
  * (generated in FP64 on the GPU, rounded to FP32) and synchronises once.
@@ -137,7 +143,8 @@ const char *fft_status_string(fft_status_t status);
  */
 fft_status_t fft_plan(fft_plan_t *out, int N, int64_t batch, int direction);
 
-/* As fft_plan with a precision (fft_precision_t) and FFT_FLAG_* flags.
+/* As fft_plan with a precision (fft_precision_t) and FFT_FLAG_* flags
+ * (N > 16384: FP32 only, FFT_FLAG_FORCE_SINGLE_CTA is FFT_ERR_NOT_SUPPORTED).
  * The tensor-core precisions support N in {256, 4096, 16384} only
  * (FFT_ERR_NOT_SUPPORTED otherwise). */
 fft_status_t fft_plan_ex(fft_plan_t *out, int N, int64_t batch, int direction,
@@ -163,7 +170,8 @@ fft_status_t fft_plan_config(fft_plan_t *out, int N, int64_t batch, int directio
 
 /*
  * fft_exec — run the plan on device buffers.
- * in, out: device pointers to batch*N float2 each (see layout above), 16-byte
+ * in, out: device pointers to batch*N float2 each (see layout above; batch*N
+ * FP16 pairs, 4 bytes each, for FFT_PREC_FP16_STORAGE), 16-byte
  * aligned; in == out is allowed, partial overlap is FFT_ERR_INVALID_VALUE.
  * For a ragged plan, in and out are the packed base pointers the plan's
  * offsets index.  stream: cudaStream_t or NULL.  Asynchronous.

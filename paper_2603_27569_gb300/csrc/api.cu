@@ -24,6 +24,7 @@
 
 #include "column.cuh"
 #include "cluster.cuh"
+#include "halfio.cuh"
 #include "staged.cuh"
 #include "plan.h"
 
@@ -266,6 +267,20 @@ fft_status_t exec_rows(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t
     return launch_split2(pl->k_single, pl->direction, in, out, pl->d_tw + pl->tw_single,
                          pl->d_tw + pl->tw_big, rows, pl->scale, st);
   }
+  if (pl->path == FFT_PATH_SINGLE_CTA && pl->k_single->kind == KIND_HALFIO) {
+    HalfArgs a;
+    a.in = (const __half2 *)in;
+    a.out = (__half2 *)out;
+    a.tw = pl->d_tw + pl->tw_single;
+    a.batch = rows;
+    a.scale = pl->scale;
+    const int64_t grid = (rows + pl->k_single->TB - 1) / pl->k_single->TB;
+    if (grid > 0x7fffffffLL) return FFT_ERR_INVALID_SIZE;
+    void *args[] = {&a};
+    FFTGB_CUDA(cudaLaunchKernel(pl->k_single->fn[pl->direction > 0 ? 1 : 0], dim3((unsigned)grid),
+                                dim3(pl->k_single->threads), args, pl->k_single->smem, st));
+    return FFT_OK;
+  }
   if (pl->path == FFT_PATH_SINGLE_CTA && pl->k_single->kind == KIND_STAGED) {
     return launch_staged(pl->k_single, pl->direction, in, out, pl->d_tw + pl->tw_single, rows,
                          pl->scale, pl->grid_ctas, pl->d_status, st);
@@ -310,6 +325,16 @@ fft_status_t exec_rows(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t
 }
 
 static bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Bytes per stored point: 8 (complex64), 4 for FP16 storage.
+static int64_t elem_bytes(const fft_plan_impl *pl) {
+  return pl->precision == FFT_PREC_FP16_STORAGE ? 4 : (int64_t)sizeof(float2);
+}
+
+// Largest N: single CTA (the whole row in registers + shared memory), and
+// overall (two-phase four-step with both factors <= 256).
+constexpr int kMaxSingleN = 16384;
+constexpr int kMaxN = 65536;
 
 // Built-in launch shape of the single-CTA path: one CTA per tile (measured
 // faster than the persistent shape for every N up to 8192 on GB300; the
@@ -441,14 +466,22 @@ static fft_status_t plan_common(fft_plan_t *out, int N, int64_t batch, int direc
                                 int precision, int flags, const fft_config_t *cfg) {
   if (!out) return FFT_ERR_INVALID_VALUE;
   *out = nullptr;
-  if (!is_pow2(N) || N < 2 || N > 16384 || batch < 0) return FFT_ERR_INVALID_SIZE;
+  if (!is_pow2(N) || N < 2 || N > kMaxN || batch < 0) return FFT_ERR_INVALID_SIZE;
   if (direction != FFT_FORWARD && direction != FFT_INVERSE) return FFT_ERR_INVALID_VALUE;
-  if (precision < FFT_PREC_FP32 || precision > FFT_PREC_BF16X2) return FFT_ERR_INVALID_VALUE;
+  if (precision < FFT_PREC_FP32 || precision > FFT_PREC_FP16_STORAGE) return FFT_ERR_INVALID_VALUE;
   if (flags & ~(FFT_FLAG_UNNORMALIZED_INVERSE | FFT_FLAG_FORCE_SINGLE_CTA |
                 FFT_FLAG_FORCE_FOURSTEP | FFT_FLAG_NO_AUTOTUNE_CACHE | FFT_FLAG_ADJOINT))
     return FFT_ERR_INVALID_VALUE;
   if ((flags & FFT_FLAG_FORCE_SINGLE_CTA) && (flags & FFT_FLAG_FORCE_FOURSTEP))
     return FFT_ERR_INVALID_VALUE;
+  // Beyond one CTA's reach (N > 16384) only the two-phase four-step runs
+  // (synthesis rule 3 of Sec. IV-D, one level: N = n1 * n2, n1, n2 <= 256).
+  if (N > kMaxSingleN) {
+    if (precision != FFT_PREC_FP32 || (flags & FFT_FLAG_FORCE_SINGLE_CTA))
+      return FFT_ERR_NOT_SUPPORTED;
+    if (cfg && cfg->path != FFT_PATH_FOURSTEP) return FFT_ERR_NOT_SUPPORTED;
+    flags |= FFT_FLAG_FORCE_FOURSTEP;
+  }
   fft_plan_s *h = new (std::nothrow) fft_plan_s;
   if (!h) return FFT_ERR_ALLOC;
   fft_plan_impl *pl = &h->impl;
@@ -494,6 +527,11 @@ static fft_status_t plan_common(fft_plan_t *out, int N, int64_t batch, int direc
       } else {
         s = FFT_ERR_INVALID_VALUE;
       }
+    } else if (precision == FFT_PREC_FP16_STORAGE) {
+      const KernelEntry *k = nullptr;
+      for (const auto &e : kernel_registry())
+        if (e.kind == KIND_HALFIO && e.N == N) k = &e;
+      s = k ? plan_single(pl, k, 0) : FFT_ERR_NOT_SUPPORTED;
     } else if (precision != FFT_PREC_FP32) {
       s = tc_plan(pl);
     } else if (flags & FFT_FLAG_FORCE_FOURSTEP) {
@@ -550,7 +588,7 @@ int fft_list_configs(int N, fft_config_t *out, int capacity) {
     if (out && n < capacity) out[n] = c;
     ++n;
   };
-  if (!is_pow2(N) || N < 2 || N > 16384) return 0;
+  if (!is_pow2(N) || N < 2 || N > kMaxN) return 0;
   for (const auto &e : kernel_registry()) {
     if (e.kind != KIND_STOCKHAM || e.N != N) continue;
     for (int shape : {0, -1}) {
@@ -634,7 +672,7 @@ fft_status_t fft_exec(fft_plan_t plan, const void *in, void *out, void *stream) 
   }
   if (pl->path == FFT_PATH_FILTER) return FFT_ERR_INVALID_VALUE;  // use fft_filter_forward
   if (pl->batch == 0) return FFT_OK;
-  fft_status_t s = check_buffers(in, out, (int64_t)sizeof(float2) * pl->N * pl->batch);
+  fft_status_t s = check_buffers(in, out, elem_bytes(pl) * pl->N * pl->batch);
   if (s != FFT_OK) return s;
   return exec_rows(pl, (const float2 *)in, (float2 *)out, pl->batch, (cudaStream_t)stream);
 }
@@ -646,7 +684,7 @@ fft_status_t fft_exec_host(fft_plan_t plan, const void *host_in, void *host_out,
   if (pl->batch == 0) return FFT_OK;
   if (!host_in || !host_out) return FFT_ERR_INVALID_VALUE;
   cudaStream_t st = (cudaStream_t)stream;
-  const int64_t row_bytes = (int64_t)sizeof(float2) * pl->N;
+  const int64_t row_bytes = elem_bytes(pl) * pl->N;
   // Chunks of about 32 MiB; two input and two output staging slots.
   if (!pl->d_stage) {
     int64_t rows = std::max<int64_t>(1, (32ll << 20) / row_bytes);
@@ -661,8 +699,10 @@ fft_status_t fft_exec_host(fft_plan_t plan, const void *host_in, void *host_out,
   }
   const int64_t R = pl->stage_rows;
   const int64_t nchunk = (pl->batch + R - 1) / R;
-  float2 *slot_in[2] = {pl->d_stage, pl->d_stage + R * pl->N};
-  float2 *slot_out[2] = {pl->d_stage + 2 * R * pl->N, pl->d_stage + 3 * R * pl->N};
+  char *stage = (char *)pl->d_stage;
+  float2 *slot_in[2] = {(float2 *)stage, (float2 *)(stage + R * row_bytes)};
+  float2 *slot_out[2] = {(float2 *)(stage + 2 * R * row_bytes),
+                         (float2 *)(stage + 3 * R * row_bytes)};
   cudaEvent_t ev_start, ev_in[2], ev_done[2], ev_out[2];
   FFTGB_CUDA(cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming));
   for (int i = 0; i < 2; ++i) {

@@ -2,6 +2,7 @@
 #pragma once
 #include "cluster.cuh"
 #include "column.cuh"
+#include "halfio.cuh"
 #include "registry.h"
 #include "staged.cuh"
 #include "stockham.cuh"
@@ -69,6 +70,23 @@ inline KernelEntry split2_entry() {
   return e;
 }
 
+template <int N, int P, int TB, int TWM, class SC>
+inline KernelEntry half_entry() {
+  KernelEntry e{};
+  e.kind = KIND_HALFIO;
+  e.N = N;
+  e.P = P;
+  e.TB = TB;
+  e.threads = TB * (N / P);
+  e.smem = sizeof(float2) * (size_t)TB * N;
+  fill_radix<SC>(e);
+  e.is_default = 1;
+  e.twm = TWM;
+  e.fn[0] = (const void *)&stockham_half_kernel<N, P, TB, -1, SC, TWM>;
+  e.fn[1] = (const void *)&stockham_half_kernel<N, P, TB, +1, SC, TWM>;
+  return e;
+}
+
 template <int L, int P, int C, int VAR, int DEF, class SC>
 inline KernelEntry column_entry() {
   KernelEntry e{};
@@ -112,6 +130,10 @@ inline KernelEntry column_entry() {
       ::fftgb::split2_entry<N, P, 0, DEF == 1, ::fftgb::Sched<__VA_ARGS__>>()); \
   static ::fftgb::Registrar FFTGB_CAT(fftgb_reg_, __COUNTER__)(              \
       ::fftgb::split2_entry<N, P, 1, DEF == 2, ::fftgb::Sched<__VA_ARGS__>>())
+// FFTGB_HALF(N, P, TB, twiddle mode, radices...): FP16-storage kernel.
+#define FFTGB_HALF(N, P, TB, TWM, ...)                                       \
+  static ::fftgb::Registrar FFTGB_CAT(fftgb_reg_, __COUNTER__)(              \
+      ::fftgb::half_entry<N, P, TB, TWM, ::fftgb::Sched<__VA_ARGS__>>())
 // FFTGB_COLUMN(L, P, C, variant, is_default, radices...)
 #define FFTGB_COLUMN(L, P, C, VAR, DEF, ...)                                 \
   static ::fftgb::Registrar FFTGB_CAT(fftgb_reg_, __COUNTER__)(              \

@@ -8,7 +8,13 @@
 
 namespace fftgb {
 
-enum KernelKind { KIND_STOCKHAM = 1, KIND_COLUMN = 2, KIND_STAGED = 3, KIND_SPLIT2 = 4 };
+enum KernelKind {
+  KIND_STOCKHAM = 1,
+  KIND_COLUMN = 2,
+  KIND_STAGED = 3,
+  KIND_SPLIT2 = 4,
+  KIND_HALFIO = 5  // FP16 storage, FP32 arithmetic
+};
 
 struct KernelEntry {
   int kind;

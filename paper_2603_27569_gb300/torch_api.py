@@ -26,14 +26,16 @@ from . import _binding as B
 __all__ = ["Plan", "get_plan", "fft", "ifft", "fft_host", "SpectralFilter",
            "spectral_filter", "clear_plan_cache"]
 
-_PREC = {"fp32": B.FFT_PREC_FP32, "fp16x2": B.FFT_PREC_FP16X2, "bf16x2": B.FFT_PREC_BF16X2}
+_PREC = {"fp32": B.FFT_PREC_FP32, "fp16x2": B.FFT_PREC_FP16X2, "bf16x2": B.FFT_PREC_BF16X2,
+         "fp16_storage": B.FFT_PREC_FP16_STORAGE}
 
 
-def _check_tensor(x: torch.Tensor, N: int, batch: int, what: str) -> None:
+def _check_tensor(x: torch.Tensor, N: int, batch: int, what: str,
+                  dtype=torch.complex64) -> None:
     if not isinstance(x, torch.Tensor):
         raise TypeError(f"{what} must be a torch.Tensor")
-    if x.dtype != torch.complex64:
-        raise TypeError(f"{what} must be complex64, got {x.dtype}")
+    if x.dtype != dtype:
+        raise TypeError(f"{what} must be {dtype}, got {x.dtype}")
     if not x.is_contiguous():
         raise ValueError(f"{what} must be contiguous")
     if x.numel() != N * batch:
@@ -58,14 +60,19 @@ class Plan:
     def __call__(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None):
         return self.exec(x, out, stream)
 
+    @property
+    def dtype(self):
+        """complex64, or torch.complex32 (FP16 pairs) for FP16 storage."""
+        return torch.complex32 if self.precision == B.FFT_PREC_FP16_STORAGE else torch.complex64
+
     def exec(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None):
         if not x.is_cuda or x.device != self.device:
             raise ValueError(f"input must live on {self.device}")
-        _check_tensor(x, self.N, self.batch, "input")
+        _check_tensor(x, self.N, self.batch, "input", self.dtype)
         if out is None:
             out = torch.empty_like(x)
         else:
-            _check_tensor(out, self.N, self.batch, "output")
+            _check_tensor(out, self.N, self.batch, "output", self.dtype)
         st = torch.cuda.current_stream(self.device) if stream is None else stream
         B.fft_exec(self.handle, x, out, st)
         return out
@@ -74,11 +81,11 @@ class Plan:
         """Transform a host (ideally pinned) complex64 tensor; returns a host tensor."""
         if x.is_cuda:
             raise ValueError("exec_host takes a host tensor")
-        _check_tensor(x, self.N, self.batch, "input")
+        _check_tensor(x, self.N, self.batch, "input", self.dtype)
         if out is None:
             out = torch.empty_like(x, pin_memory=x.is_pinned())
         else:
-            _check_tensor(out, self.N, self.batch, "output")
+            _check_tensor(out, self.N, self.batch, "output", self.dtype)
         with torch.cuda.device(self.device):
             st = torch.cuda.current_stream(self.device) if stream is None else stream
             B.fft_exec_host(self.handle, x, out, st)

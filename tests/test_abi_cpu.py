@@ -67,7 +67,7 @@ def _plan_ex(L, N, batch, direction, prec=0, flags=0):
     return rc, h.value
 
 
-@pytest.mark.parametrize("N", [0, 1, 3, 12, 100, 32768, 1 << 20])
+@pytest.mark.parametrize("N", [0, 1, 3, 12, 100, 131072, 1 << 20])
 def test_plan_rejects_bad_sizes(L, N):
     rc, h = _plan_ex(L, N, 4, -1)
     assert rc == INVALID_SIZE and h is None
@@ -81,6 +81,8 @@ def test_plan_rejects_bad_arguments(L):
     assert _plan_ex(L, 256, 4, -1, flags=0x100)[0] == INVALID_VALUE
     assert _plan_ex(L, 256, 4, -1, flags=fg.FFT_FLAG_FORCE_FOURSTEP | fg.FFT_FLAG_FORCE_SINGLE_CTA)[0] \
         == INVALID_VALUE
+    assert _plan_ex(L, 32768, 4, -1, flags=fg.FFT_FLAG_FORCE_SINGLE_CTA)[0] == 7
+    assert _plan_ex(L, 32768, 4, -1, prec=fg.FFT_PREC_FP16X2)[0] == 7
     assert L.fft_plan_ex(None, 256, 4, -1, 0, 0) == INVALID_VALUE
 
 
@@ -114,7 +116,10 @@ def test_configs_listed_for_every_supported_size(L):
             else:
                 assert prod == N // c["n1"] and N % c["n1"] == 0
     assert fg.fft_list_configs(12) == []
-    assert fg.fft_list_configs(32768) == []
+    assert fg.fft_list_configs(131072) == []
+    for N in (32768, 65536):   # beyond one CTA: two-phase four-step only
+        cfgs = fg.fft_list_configs(N)
+        assert cfgs and all(c["path"] == fg.FFT_PATH_FOURSTEP for c in cfgs)
     for N in (8192, 16384):
         assert any(c["path"] == fg.FFT_PATH_FOURSTEP for c in fg.fft_list_configs(N))
 

@@ -268,3 +268,13 @@ def test_host_buffer_exec_matches_device_exec(N, flags):
     plan.close()
     assert np.array_equal(dev.view(np.uint32), host.view(np.uint32))
     check(x[:4], host[:4], fg.FFT_FORWARD)
+
+
+@pytest.mark.parametrize("N", [32768, 65536])
+@pytest.mark.parametrize("direction", [fg.FFT_FORWARD, fg.FFT_INVERSE])
+def test_beyond_one_cta_fourstep(N, direction):
+    # N > 16384: the two-phase four-step (n1, n2 <= 256) is the only path
+    x = synth.gaussian((3, N), seed=N)
+    y, info = run(x, direction)
+    assert info["path"] == fg.FFT_PATH_FOURSTEP and info["n1"] * info["n2"] == N
+    check(x, y, direction)
