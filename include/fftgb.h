@@ -101,6 +101,7 @@ typedef struct {
     int grid_ctas;          /* CTAs launched per exec (0 = one per tile)      */
     int tma_slabs;          /* as in fft_config_t                              */
     int cluster_split;      /* as in fft_config_t                              */
+    int l2_chunk_rows;      /* as in fft_config_t                              */
 } fft_plan_info_t;
 
 /* One compiled execution configuration (see fft_list_configs). */
@@ -123,6 +124,12 @@ typedef struct {
     int cluster_split;      /* 2: each row on a 2-CTA thread-block cluster (halves
                                of N/2 points combined through distributed shared
                                memory); 0: one CTA per row                      */
+    int l2_chunk_rows;      /* four-step with n1 == n2 only.  > 0: both phases in
+                               one persistent launch; rows are cut into chunks of
+                               this many rows whose intermediate stays in a ring
+                               of L2-sized scratch slots (HBM traffic 16 N B per
+                               row instead of 32 N B); 0: two launches through
+                               a scratch copy of the whole batch               */
 } fft_config_t;
 
 /* Human-readable name of a status code (static string, never NULL). */

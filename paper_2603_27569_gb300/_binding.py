@@ -65,7 +65,7 @@ class PlanInfo(ctypes.Structure):
         ("radix", ctypes.c_int * 8), ("n1", ctypes.c_int), ("n2", ctypes.c_int),
         ("scratch_bytes", ctypes.c_int64), ("twiddle_mode", ctypes.c_int),
         ("grid_ctas", ctypes.c_int), ("tma_slabs", ctypes.c_int),
-        ("cluster_split", ctypes.c_int),
+        ("cluster_split", ctypes.c_int), ("l2_chunk_rows", ctypes.c_int),
     ]
 
     def as_dict(self) -> dict:
@@ -81,6 +81,7 @@ class Config(ctypes.Structure):
         ("num_passes", ctypes.c_int), ("radix", ctypes.c_int * 8), ("n1", ctypes.c_int),
         ("twiddle_mode", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
         ("tma_slabs", ctypes.c_int), ("cluster_split", ctypes.c_int),
+        ("l2_chunk_rows", ctypes.c_int),
     ]
 
     def as_dict(self) -> dict:

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "column.cuh"
+#include "fourstep_l2.cuh"
 #include "cluster.cuh"
 #include "halfio.cuh"
 #include "staged.cuh"
@@ -260,6 +261,40 @@ static fft_status_t launch_column(const KernelEntry *k, int dir, const ColumnArg
   return FFT_OK;
 }
 
+// Single-launch four-step (fourstep_l2.cuh).  Batches whose work-item count
+// would pass 2^30 run as several launches of whole chunks.
+static fft_status_t launch_fourstep_l2(fft_plan_impl *pl, const float2 *in, float2 *out,
+                                       int64_t rows, cudaStream_t st) {
+  const KernelEntry *k = pl->k_l2;
+  const int64_t R = pl->l2_rows;
+  const int64_t tiles_per_row = pl->n1 / k->TB;
+  const int64_t max_chunks = std::max<int64_t>(1, (1ll << 29) / (R * tiles_per_row)) - pl->l2_lag;
+  if (max_chunks < 1) return FFT_ERR_INVALID_SIZE;
+  for (int64_t r0 = 0; r0 < rows; r0 += max_chunks * R) {
+    const int64_t nr = std::min(max_chunks * R, rows - r0);
+    FourstepL2Args a;
+    a.in = in + r0 * pl->N;
+    a.out = out + r0 * pl->N;
+    a.ring = pl->d_scratch;
+    a.tw = pl->d_tw + pl->tw_col1;
+    a.tw_big = pl->d_tw + pl->tw_big;
+    a.counters = pl->d_l2cnt;
+    a.status = pl->d_status;
+    a.batch = nr;
+    a.chunk_rows = (int)R;
+    a.nchunks = (int)((nr + R - 1) / R);
+    a.slots = std::min(pl->l2_slots, a.nchunks);
+    a.lag = pl->l2_lag;
+    a.scale = pl->scale;
+    const int64_t items = (int64_t)(a.nchunks + a.lag) * 2 * R * tiles_per_row;
+    const int64_t grid = std::min(pl->l2_grid, items);
+    void *args[] = {&a};
+    FFTGB_CUDA(cudaLaunchKernel(k->fn[pl->direction > 0 ? 1 : 0], dim3((unsigned)grid),
+                                dim3(k->threads), args, k->smem, st));
+  }
+  return FFT_OK;
+}
+
 fft_status_t exec_rows(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t rows,
                        cudaStream_t st) {
   if (rows <= 0) return FFT_OK;
@@ -289,6 +324,7 @@ fft_status_t exec_rows(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t
     return launch_stockham(pl->k_single, pl->direction, in, out, pl->d_tw + pl->tw_single, rows,
                            pl->scale, pl->grid_ctas, st);
   }
+  if (pl->path == FFT_PATH_FOURSTEP && pl->k_l2) return launch_fourstep_l2(pl, in, out, rows, st);
   if (pl->path == FFT_PATH_FOURSTEP) {
     ColumnArgs c1{};
     c1.in = in;
@@ -363,25 +399,61 @@ static bool fourstep_split(int N, int want_n1, int *n1, int *n2) {
   return true;
 }
 
-static fft_status_t plan_fourstep(fft_plan_impl *pl, int want_n1) {
+// Largest chunk of the single-launch four-step (rows per chunk).
+constexpr int kMaxL2Rows = 4096;
+
+// Ring geometry of the single-launch four-step.  Claims run one item ahead
+// of the work, so up to F = 2 * grid items are claimed but unfinished.  A
+// phase-2 tile of chunk c is claimed l2_lag rounds after chunk c's phase-1
+// tiles, and a phase-1 tile of chunk c reuses the slot of chunk c - slots,
+// whose phase-2 tiles were claimed slots - lag rounds earlier; both distances
+// are F items plus a round of margin, so neither wait normally spins.
+// Deadlock freedom needs slots > lag.
+static void l2_geometry(fft_plan_impl *pl) {
+  const int64_t round = 2 * (int64_t)pl->l2_rows * (pl->n1 / pl->k_l2->TB);
+  const int64_t f = 2 * std::max<int64_t>(1, pl->l2_grid);
+  const int d = (int)((f + round - 1) / round) + 1;
+  pl->l2_lag = d;
+  pl->l2_slots = 2 * d;
+}
+
+static fft_status_t plan_fourstep(fft_plan_impl *pl, int want_n1, int l2_rows) {
   int n1, n2;
   if (!fourstep_split(pl->N, want_n1, &n1, &n2)) return FFT_ERR_NOT_SUPPORTED;
+  if (l2_rows < 0 || l2_rows > kMaxL2Rows) return FFT_ERR_INVALID_VALUE;
   pl->path = FFT_PATH_FOURSTEP;
   pl->n1 = n1;
   pl->n2 = n2;
-  pl->k_col1 = default_column(n2, 1);
-  pl->k_col2 = default_column(n1, 0);
-  fft_status_t s = ensure_smem_attr(pl->k_col1);
-  if (s == FFT_OK) s = ensure_smem_attr(pl->k_col2);
-  if (s != FFT_OK) return s;
   int64_t off = 0;
   std::vector<TwSeg> segs;
-  pl->tw_col1 = off;
-  auto a = pass_segments(*pl->k_col1, off);
-  segs.insert(segs.end(), a.begin(), a.end());
-  pl->tw_col2 = off;
-  auto b = pass_segments(*pl->k_col2, off);
-  segs.insert(segs.end(), b.begin(), b.end());
+  fft_status_t s = FFT_OK;
+  if (l2_rows > 0) {
+    if (n1 != n2) return FFT_ERR_NOT_SUPPORTED;
+    for (const auto &e : kernel_registry())
+      if (e.kind == KIND_FOURSTEP_L2 && e.N == n1) pl->k_l2 = &e;
+    if (!pl->k_l2) return FFT_ERR_NOT_SUPPORTED;
+    s = ensure_smem_attr(pl->k_l2);
+    if (s != FFT_OK) return s;
+    pl->l2_rows = l2_rows;
+    pl->l2_grid = persistent_grid(pl->k_l2, -1);
+    if (pl->l2_grid <= 0) return FFT_ERR_CUDA;
+    l2_geometry(pl);
+    pl->tw_col1 = pl->tw_col2 = off;
+    auto a = pass_segments(*pl->k_l2, off);
+    segs.insert(segs.end(), a.begin(), a.end());
+  } else {
+    pl->k_col1 = default_column(n2, 1);
+    pl->k_col2 = default_column(n1, 0);
+    s = ensure_smem_attr(pl->k_col1);
+    if (s == FFT_OK) s = ensure_smem_attr(pl->k_col2);
+    if (s != FFT_OK) return s;
+    pl->tw_col1 = off;
+    auto a = pass_segments(*pl->k_col1, off);
+    segs.insert(segs.end(), a.begin(), a.end());
+    pl->tw_col2 = off;
+    auto b = pass_segments(*pl->k_col2, off);
+    segs.insert(segs.end(), b.begin(), b.end());
+  }
   pl->tw_big = off;
   TwSeg big;
   big.offset = off;
@@ -393,7 +465,21 @@ static fft_status_t plan_fourstep(fft_plan_impl *pl, int want_n1) {
   segs.push_back(big);
   s = build_twiddles(pl, segs);
   if (s != FFT_OK) return s;
-  pl->scratch_bytes = (int64_t)sizeof(float2) * pl->N * pl->batch;
+  if (pl->k_l2) {
+    // ring slots (no more than the batch has chunks) + the launch counters
+    const int64_t nch = (pl->batch + l2_rows - 1) / l2_rows;
+    const int64_t slots = std::min<int64_t>(pl->l2_slots, nch);
+    pl->scratch_bytes = (int64_t)sizeof(float2) * pl->N * l2_rows * slots;
+    const int64_t ncnt = 2 + 2 * std::max<int64_t>(nch, 1);
+    if (cudaMalloc(&pl->d_l2cnt, sizeof(unsigned) * (size_t)ncnt) != cudaSuccess) {
+      cudaGetLastError();
+      return FFT_ERR_ALLOC;
+    }
+    if (cudaMemset(pl->d_l2cnt, 0, sizeof(unsigned) * (size_t)ncnt) != cudaSuccess)
+      return FFT_ERR_CUDA;
+  } else {
+    pl->scratch_bytes = (int64_t)sizeof(float2) * pl->N * pl->batch;
+  }
   if (pl->scratch_bytes > 0) {
     if (cudaMalloc(&pl->d_scratch, (size_t)pl->scratch_bytes) != cudaSuccess) {
       cudaGetLastError();
@@ -436,6 +522,7 @@ static void free_plan(fft_plan_impl *pl) {
   if (pl->tc) tc_destroy(pl);
   if (pl->d_tw) cudaFree(pl->d_tw);
   if (pl->d_scratch) cudaFree(pl->d_scratch);
+  if (pl->d_l2cnt) cudaFree(pl->d_l2cnt);
   if (pl->d_status) cudaFree(pl->d_status);
   if (pl->d_stage) cudaFree(pl->d_stage);
   if (pl->s_h2d) cudaStreamDestroy(pl->s_h2d);
@@ -473,6 +560,9 @@ static fft_status_t plan_common(fft_plan_t *out, int N, int64_t batch, int direc
                 FFT_FLAG_FORCE_FOURSTEP | FFT_FLAG_NO_AUTOTUNE_CACHE | FFT_FLAG_ADJOINT))
     return FFT_ERR_INVALID_VALUE;
   if ((flags & FFT_FLAG_FORCE_SINGLE_CTA) && (flags & FFT_FLAG_FORCE_FOURSTEP))
+    return FFT_ERR_INVALID_VALUE;
+  if (cfg && (cfg->l2_chunk_rows < 0 || cfg->l2_chunk_rows > kMaxL2Rows ||
+              (cfg->l2_chunk_rows > 0 && cfg->path != FFT_PATH_FOURSTEP)))
     return FFT_ERR_INVALID_VALUE;
   // Beyond one CTA's reach (N > 16384) only the two-phase four-step runs
   // (synthesis rule 3 of Sec. IV-D, one level: N = n1 * n2, n1, n2 <= 256).
@@ -512,7 +602,7 @@ static fft_status_t plan_common(fft_plan_t *out, int N, int64_t batch, int direc
   if (s == FFT_OK) {
     if (cfg) {
       if (cfg->path == FFT_PATH_FOURSTEP) {
-        s = plan_fourstep(pl, cfg->n1);
+        s = plan_fourstep(pl, cfg->n1, cfg->l2_chunk_rows);
       } else if (cfg->path == FFT_PATH_SINGLE_CTA) {
         const KernelEntry *k =
             cfg->cluster_split == 2
@@ -535,7 +625,7 @@ static fft_status_t plan_common(fft_plan_t *out, int N, int64_t batch, int direc
     } else if (precision != FFT_PREC_FP32) {
       s = tc_plan(pl);
     } else if (flags & FFT_FLAG_FORCE_FOURSTEP) {
-      s = plan_fourstep(pl, 0);
+      s = plan_fourstep(pl, 0, 0);
     } else if (flags & FFT_FLAG_FORCE_SINGLE_CTA) {
       s = plan_single(pl, default_stockham(N), kDefaultCtasPerSm);
     } else {
@@ -543,7 +633,7 @@ static fft_status_t plan_common(fft_plan_t *out, int N, int64_t batch, int direc
       bool have = !(flags & FFT_FLAG_NO_AUTOTUNE_CACHE) &&
                   tune_lookup(N, pl->direction, precision, &tc);
       if (have && tc.path == FFT_PATH_FOURSTEP) {
-        s = plan_fourstep(pl, tc.n1);
+        s = plan_fourstep(pl, tc.n1, tc.l2rows);
         if (s == FFT_ERR_NOT_SUPPORTED) have = false;
       } else if (have) {
         const KernelEntry *k =
@@ -648,6 +738,24 @@ int fft_list_configs(int N, fft_config_t *out, int capacity) {
     for (int i = 0; i < 8; ++i) c.radix[i] = k->radix[i];
     c.n1 = n1;
     emit(c);
+    if (n1 != n2) continue;
+    for (const auto &e : kernel_registry()) {
+      if (e.kind != KIND_FOURSTEP_L2 || e.N != n1) continue;
+      for (int rows : {8, 16, 32, 64}) {
+        fft_config_t d;
+        memset(&d, 0, sizeof(d));
+        d.path = FFT_PATH_FOURSTEP;
+        d.points_per_thread = e.P;
+        d.transforms_per_cta = e.TB;
+        d.threads_per_cta = e.threads;
+        d.num_passes = e.npass;
+        for (int i = 0; i < 8; ++i) d.radix[i] = e.radix[i];
+        d.n1 = n1;
+        d.ctas_per_sm = -1;
+        d.l2_chunk_rows = rows;
+        emit(d);
+      }
+    }
   }
   return n;
 }
@@ -768,7 +876,7 @@ fft_status_t fft_plan_info(fft_plan_t plan, fft_plan_info_t *info) {
   info->path = pl->path;
   info->scratch_bytes = pl->scratch_bytes;
   const KernelEntry *k = pl->path == FFT_PATH_SINGLE_CTA ? pl->k_single
-                         : pl->path == FFT_PATH_FOURSTEP ? pl->k_col1
+                         : pl->path == FFT_PATH_FOURSTEP ? (pl->k_l2 ? pl->k_l2 : pl->k_col1)
                                                          : nullptr;
   if (k) {
     info->points_per_thread = k->P;
@@ -784,6 +892,8 @@ fft_status_t fft_plan_info(fft_plan_t plan, fft_plan_info_t *info) {
   info->tma_slabs = pl->path == FFT_PATH_SINGLE_CTA ? pl->k_single->slabs : 0;
   info->cluster_split =
       (pl->path == FFT_PATH_SINGLE_CTA && pl->k_single->kind == KIND_SPLIT2) ? 2 : 0;
+  info->l2_chunk_rows = pl->l2_rows;
+  if (pl->k_l2) info->grid_ctas = (int)pl->l2_grid;
   return FFT_OK;
 }
 

@@ -67,9 +67,9 @@ fft_status_t write_json(const char *path) {
     const auto &c = kv.second.choice;
     fprintf(f, "%s  {\"N\": %d, \"direction\": %d, \"precision\": %d, \"path\": %d, \"P\": %d, "
                "\"TB\": %d, \"n1\": %d, \"twm\": %d, \"ctas_per_sm\": %d, \"slabs\": %d, "
-               "\"split\": %d, \"radix\": [",
+               "\"split\": %d, \"l2rows\": %d, \"radix\": [",
             first ? "" : ",\n", kv.first.N, kv.first.dir, kv.first.prec, c.path, c.P, c.TB, c.n1,
-            c.twm, c.ctas_per_sm, c.slabs, c.split);
+            c.twm, c.ctas_per_sm, c.slabs, c.split, c.l2rows);
     for (int i = 0; i < c.npass; ++i) fprintf(f, "%s%d", i ? ", " : "", c.radix[i]);
     fprintf(f, "], \"us\": %.3f, \"batch\": %lld}", kv.second.us, (long long)kv.second.batch);
     first = false;
@@ -117,6 +117,7 @@ fft_status_t load_json(const char *path) {
               read_int(s, "ctas_per_sm", b, e, &en.choice.ctas_per_sm) &&
               read_int(s, "slabs", b, e, &en.choice.slabs) &&
               read_int(s, "split", b, e, &en.choice.split);
+    if (!read_int(s, "l2rows", b, e, &en.choice.l2rows)) en.choice.l2rows = 0;  // optional
     size_t r = s.find("\"radix\": [", b);
     if (ok && r != std::string::npos && r < e) {
       const char *q = s.c_str() + r + 10;
@@ -216,6 +217,7 @@ fft_status_t fft_autotune(int N, int direction, int precision, int64_t batch,
       best.ctas_per_sm = c.ctas_per_sm;
       best.slabs = c.tma_slabs;
       best.split = c.cluster_split;
+      best.l2rows = c.l2_chunk_rows;
     }
   }
   cudaEventDestroy(e0);

@@ -2,6 +2,7 @@
 #pragma once
 #include "cluster.cuh"
 #include "column.cuh"
+#include "fourstep_l2.cuh"
 #include "halfio.cuh"
 #include "registry.h"
 #include "staged.cuh"
@@ -104,6 +105,23 @@ inline KernelEntry column_entry() {
   return e;
 }
 
+template <int L, int P, int C, class SC>
+inline KernelEntry fourstep_l2_entry() {
+  KernelEntry e{};
+  e.kind = KIND_FOURSTEP_L2;
+  e.N = L;
+  e.P = P;
+  e.TB = C;
+  e.threads = C * (L / P);
+  e.smem = sizeof(float2) * (size_t)L * (C + 1);
+  fill_radix<SC>(e);
+  e.is_default = 0;
+  e.variant = 0;
+  e.fn[0] = (const void *)&fourstep_l2_kernel<L, P, C, -1, SC>;
+  e.fn[1] = (const void *)&fourstep_l2_kernel<L, P, C, +1, SC>;
+  return e;
+}
+
 }  // namespace fftgb
 
 #define FFTGB_CAT2(a, b) a##b
@@ -138,3 +156,7 @@ inline KernelEntry column_entry() {
 #define FFTGB_COLUMN(L, P, C, VAR, DEF, ...)                                 \
   static ::fftgb::Registrar FFTGB_CAT(fftgb_reg_, __COUNTER__)(              \
       ::fftgb::column_entry<L, P, C, VAR, DEF, ::fftgb::Sched<__VA_ARGS__>>())
+// FFTGB_FOURSTEP_L2(L, P, C, radices of L...): N = L * L in one launch.
+#define FFTGB_FOURSTEP_L2(L, P, C, ...)                                      \
+  static ::fftgb::Registrar FFTGB_CAT(fftgb_reg_, __COUNTER__)(              \
+      ::fftgb::fourstep_l2_entry<L, P, C, ::fftgb::Sched<__VA_ARGS__>>())

@@ -38,6 +38,13 @@ struct fft_plan_impl {
   // four-step path: phase-1 and phase-2 column kernels, split N = n1 * n2
   const KernelEntry *k_col1 = nullptr, *k_col2 = nullptr;
   int n1 = 0, n2 = 0;
+  // four-step in one launch with the intermediate in an L2 ring (n1 == n2):
+  // chunks of l2_rows rows, l2_slots ring slots, phase 2 of a chunk claimed
+  // l2_lag rounds after its phase 1; d_l2cnt = the launch's work counters
+  const KernelEntry *k_l2 = nullptr;
+  int l2_rows = 0, l2_lag = 0, l2_slots = 0;
+  int64_t l2_grid = 0;
+  unsigned *d_l2cnt = nullptr;
   // twiddles
   float2 *d_tw = nullptr;
   int64_t tw_count = 0;
@@ -88,6 +95,7 @@ struct TuneChoice {
   int ctas_per_sm;          // 0 / -1 / k (see fft_config_t)
   int slabs;                // TMA-staged ring size (0: direct loads)
   int split;                // 2: cluster-split kernel
+  int l2rows;               // four-step in one launch, chunks of this many rows
 };
 bool tune_lookup(int N, int direction, int precision, TuneChoice *out);
 

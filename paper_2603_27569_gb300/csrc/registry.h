@@ -13,12 +13,13 @@ enum KernelKind {
   KIND_COLUMN = 2,
   KIND_STAGED = 3,
   KIND_SPLIT2 = 4,
-  KIND_HALFIO = 5  // FP16 storage, FP32 arithmetic
+  KIND_HALFIO = 5,      // FP16 storage, FP32 arithmetic
+  KIND_FOURSTEP_L2 = 6  // both four-step phases in one persistent launch (N = L * L)
 };
 
 struct KernelEntry {
   int kind;
-  int N;          // transform length (L for column kernels; the full N for split2)
+  int N;          // transform length (L for column and L2 four-step kernels; the full N for split2)
   int P;          // complex points per thread
   int TB;         // rows per CTA (single-CTA) / columns per CTA (column)
   int threads;    // threads per CTA
