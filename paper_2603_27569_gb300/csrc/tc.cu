@@ -1,26 +1,35 @@
-// Split-precision tensor-core FFT: radix-16 DFT blocks as dense FP16/BF16
-// contractions with FP32 accumulation (paper Sec. V-C, Eq. 5-6, where the
-// Apple kernel maps DFT_8 onto 8x8 matrix units; here DFT_16 maps onto the
-// m16n8k16 tensor-core shape, the tcFFT idea of Sec. VIII).
+// Split-precision tensor-core FFT on the fifth-generation tensor cores
+// (tcgen05): radix-16 DFT blocks as dense FP16/BF16 contractions with FP32
+// accumulation (paper Sec. V-C, Eq. 5-6, where the Apple kernel maps DFT_8
+// onto 8x8 matrix units; here DFT_16 maps onto a 128 x 32 x 32 tcgen05.mma,
+// the tcFFT idea of Sec. VIII).
 //
-// One radix-16 Stockham stage over 16 butterflies is the real product
-//     D (16 x 32) = X^T (16 x 32) . G^T (32 x 32),
-// row b of X^T = [Re x_b(0..15), Im x_b(0..15)] (the twiddled inputs of
-// butterfly b), G = [[Fr, -Fi], [Fi, Fr]] with F = (W_16^{jk}) (conjugated for
-// the inverse), row b of D = [Re X_b(0..15), Im X_b(0..15)].  Both operands
-// are split into a high and a low 16-bit part, v = hi + lo with
-// hi = round16(v), lo = round16(v - hi), and the product is accumulated in
-// FP32 as hi.hi + hi.lo + lo.hi (lo.lo, ~2^-22 relative, is dropped).  The
-// split doubles the operand precision to ~22 bits (FP16) / ~16 bits (BF16).
+// One radix-16 Stockham stage over 128 butterflies is the real product
+//     D (128 x 32) = A (128 x 32) . G^T,
+// row m of A = the 16 twiddled inputs of one butterfly, interleaved
+// [Re x(0), Im x(0), Re x(1), ...]; G (32 x 32) the real form of F =
+// (W_16^{jk}) (conjugated for the inverse) with the same interleaving; row m
+// of D = the butterfly's 16 outputs.  Both operands are split into a high
+// and a low 16-bit part, v = hi + lo with hi = round16(v), lo = round16(v -
+// hi), and D = Ahi.Ghi^T + Ahi.Glo^T + Alo.Ghi^T is accumulated in FP32 in
+// tensor memory (lo.lo, ~2^-22 relative, is dropped): ~22-bit (FP16) or
+// ~16-bit (BF16) operands.
 //
-// Mapping: a warp owns groups of 16 butterflies; lane (g = lane / 4,
-// t = lane % 4) owns butterflies g and g + 8 of the group and their points
-// {2t, 2t+1, 2t+8, 2t+9} -- exactly the A-fragment (row g / g+8, columns
-// 2t.., 2t+8..) and accumulator (row g / g+8, columns 2t..) positions of
-// mma.m16n8k16, so no shuffles are needed.  Stages exchange through shared
-// memory like the FP32 Stockham passes; twiddles between stages are FP32
-// from the FP64-generated pass tables; N = 16384's radix-4 tail runs on the
-// CUDA cores.
+// Data path per stage: A (hi and lo planes) and G sit in shared memory in the
+// K-major, unswizzled canonical layout (core matrices of 8 rows x 16 bytes;
+// K-adjacent core matrices LBO bytes apart, 8-row groups SBO bytes apart);
+// one thread issues 6 tcgen05.mma per 128-row tile into TMEM and commits to
+// an mbarrier; every thread then reads its TMEM lane (tcgen05.ld 32x32b) --
+// one butterfly's 16 outputs -- multiplies each output by the next stage's
+// FP32 twiddle, splits it and stores it straight into the next stage's A
+// (that store is the Stockham exchange; the tensor core reads the operand).
+// Which A row holds which butterfly is a per-stage bit permutation of the
+// butterfly index, and LBO/SBO are padded (144/576 or 144/592 bytes), chosen
+// by exhaustive search on a model of the bank mapping so that every
+// exchange store is conflict-free, the first stage's row stores take the
+// minimum wavefronts and the global loads/stores touch the minimum sectors.
+// N = 16384 = 16^3 * 4 ends with a radix-4 pass in registers: each thread's
+// four TMEM tiles hold the four butterflies that feed one radix-4 butterfly.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -29,6 +38,7 @@
 #include <new>
 
 #include "plan.h"
+#include "staged.cuh"
 #include "stockham.cuh"
 
 namespace fftgb {
@@ -36,284 +46,393 @@ namespace fftgb {
 struct TcArgs {
   const float2 *in;
   float2 *out;
-  const float2 *tw;        // pass tables of the radix schedule (16,16[,16][,4])
-  const uint32_t *frag;    // B fragments: [hi/lo][kt 2][nt 4][lane 32][2] u32
+  const float2 *tw;       // pass tables of the schedule 16, 16[, 16][, 4]
+  const uint4 *bimg;      // this direction's G image: hi plane, lo plane (2 KiB each)
+  int *status;            // FFT_ERR_TIMEOUT if an MMA completion wait ran out
   long long batch;
   float scale;
 };
 
-// 16-bit split of v: hi = round(v), lo = round(v - hi), packed two per u32.
+// Per-size plan (MINB: CTAs per SM the register budget is sized for).
+// Row permutations rho_s are nibble-packed: nibble b = the
+// bit of the packed butterfly index (row-in-CTA << log2 NB | butterfly) that
+// becomes bit b of the A row at stage s.
+template <int N>
+struct TcCfg;
+template <>
+struct TcCfg<256> {
+  static constexpr int S = 2, TAIL = 0, TB = 16, NW = 8, LBO = 144, SBO = 576, MINB = 3;
+  static constexpr unsigned long long R0 = 0x45763021ull, R1 = 0x73526140ull, R2 = 0;
+};
+template <>
+struct TcCfg<4096> {
+  static constexpr int S = 3, TAIL = 0, TB = 1, NW = 8, LBO = 144, SBO = 576, MINB = 3;
+  static constexpr unsigned long long R0 = 0x76354210ull, R1 = 0x73210654ull, R2 = 0x76543102ull;
+};
+template <>
+struct TcCfg<16384> {
+  static constexpr int S = 3, TAIL = 4, TB = 1, NW = 8, LBO = 144, SBO = 592, MINB = 1;
+  static constexpr unsigned long long R0 = 0x8539064712ull, R1 = 0x4130576289ull,
+                                      R2 = 0x9876543210ull;
+};
+
+template <class C>
+__host__ __device__ constexpr unsigned long long tc_rcode(int s) {
+  return s == 0 ? C::R0 : s == 1 ? C::R1 : C::R2;
+}
+
+// v (packed butterfly index) -> row; and back.
+template <unsigned long long R, int NBITS>
+__host__ __device__ constexpr int tc_row(int v) {
+  int m = 0;
+  for (int b = 0; b < NBITS; ++b) m |= ((v >> (int)((R >> (4 * b)) & 15)) & 1) << b;
+  return m;
+}
+template <unsigned long long R, int NBITS>
+__host__ __device__ constexpr int tc_unrow(int m) {
+  int v = 0;
+  for (int b = 0; b < NBITS; ++b) v |= ((m >> b) & 1) << (int)((R >> (4 * b)) & 15);
+  return v;
+}
+// Byte offset of row m's first core-matrix row (the K-slot terms are added).
+template <int SBO>
+__host__ __device__ constexpr int tc_rowoff(int m) {
+  return (m >> 3) * SBO + (m & 7) * 16;
+}
+
+// Twiddle-table offset of pass s (s >= 1) of the schedule 16, 16, 16, 4.
+__host__ __device__ constexpr int tc_twoff(int s) { return s == 1 ? 0 : s == 2 ? 240 : 4080; }
+
+// Shared-memory bytes of the kernel for size N: A hi and lo planes, the G
+// image, the mbarrier and the TMEM address slot.
+template <int N>
+__host__ __device__ constexpr int tc_smem_bytes() {
+  return 2 * (TcCfg<N>::TB * (N / 16) / 8) * TcCfg<N>::SBO + 4096 + 16;
+}
+
+// 16-bit split of (v0, v1): hi = round(v), lo = round(v - hi), packed two per u32.
 template <int PREC>
 __device__ __forceinline__ void split2(float v0, float v1, uint32_t &hi, uint32_t &lo) {
   if constexpr (PREC == FFT_PREC_FP16X2) {
-    __half h0 = __float2half_rn(v0), h1 = __float2half_rn(v1);
-    __half l0 = __float2half_rn(v0 - __half2float(h0));
-    __half l1 = __float2half_rn(v1 - __half2float(h1));
-    __half2 H = __halves2half2(h0, h1), L = __halves2half2(l0, l1);
-    hi = *reinterpret_cast<uint32_t *>(&H);
-    lo = *reinterpret_cast<uint32_t *>(&L);
+    const __half2 H = __floats2half2_rn(v0, v1);
+    const float2 h = __half22float2(H);
+    const __half2 L = __floats2half2_rn(v0 - h.x, v1 - h.y);
+    hi = *reinterpret_cast<const uint32_t *>(&H);
+    lo = *reinterpret_cast<const uint32_t *>(&L);
   } else {
-    __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
-    __nv_bfloat16 l0 = __float2bfloat16_rn(v0 - __bfloat162float(h0));
-    __nv_bfloat16 l1 = __float2bfloat16_rn(v1 - __bfloat162float(h1));
-    __nv_bfloat162 H = __halves2bfloat162(h0, h1), L = __halves2bfloat162(l0, l1);
-    hi = *reinterpret_cast<uint32_t *>(&H);
-    lo = *reinterpret_cast<uint32_t *>(&L);
+    const __nv_bfloat162 H = __floats2bfloat162_rn(v0, v1);
+    const float2 h = __bfloat1622float2(H);
+    const __nv_bfloat162 L = __floats2bfloat162_rn(v0 - h.x, v1 - h.y);
+    hi = *reinterpret_cast<const uint32_t *>(&H);
+    lo = *reinterpret_cast<const uint32_t *>(&L);
   }
 }
 
+// Shared-memory matrix descriptor: K-major, no swizzle (layout type 0),
+// descriptor version 1 (bits 46-47).
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) |
+         ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, A/B FP16 or BF16,
+// both K-major, N = 32, M = 128.
 template <int PREC>
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
-                                         uint32_t b1) {
-  if constexpr (PREC == FFT_PREC_FP16X2) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-  } else {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+__host__ __device__ constexpr uint32_t tc_idesc() {
+  return (1u << 4) | (PREC == FFT_PREC_BF16X2 ? ((1u << 7) | (1u << 10)) : 0u) |
+         ((32u >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+}
+// 8 consecutive FP32 columns.
+__device__ __forceinline__ void tc_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tc_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Exchange after TC stage s (stride p = 16^s): this thread's butterfly (row
+// m, outputs in r) writes output j, times the stage-(s+1) twiddle, into the
+// stage-(s+1) A planes.  With butterfly i = p u + k the output lands at
+// position p (16 u + j) + k = base | j p (disjoint bits, j p < N / 16), so
+// its row is row(base) | row(j p) and its byte offset is the thread's
+// offset plus a compile-time constant per j.
+template <int N, int D, int PREC, int s>
+__device__ __forceinline__ void tc_exchange(const uint32_t (&r)[32], int m, uint8_t *Ahi,
+                                            uint8_t *Alo, const float2 *__restrict__ tw) {
+  using C = TcCfg<N>;
+  constexpr int NB = N / 16, IB = ilog2(NB), NBITS = ilog2(C::TB * NB);
+  constexpr int p = s == 0 ? 1 : s == 1 ? 16 : 256, LP = 4 * s;
+  constexpr unsigned long long RS = tc_rcode<C>(s), RN = tc_rcode<C>(s + 1);
+  static_assert(16 * p <= NB, "j p must stay below the butterfly count");
+  const int v = tc_unrow<RS, NBITS>(m);
+  const int b = v >> IB, i = v & (NB - 1);
+  const int k = i & (p - 1), u = i >> LP;
+  const int base = (u << (LP + 4)) | k;       // position of output j = 0
+  const int j2 = base >> IB;                  // the next stage's point index
+  const int m2 = tc_row<RN, NBITS>((b << IB) | (base & (NB - 1)));
+  const int off = tc_rowoff<C::SBO>(m2) + (j2 >> 2) * C::LBO + (j2 & 3) * 4;
+  const float2 *twp = tw + tc_twoff(s + 1) + (j2 > 0 ? (j2 - 1) * 16 * p : 0) + k;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    float2 x = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+    if (j2 > 0) x = cmul_dir<D>(x, __ldg(twp + j * p));
+    uint32_t hi, lo;
+    split2<PREC>(x.x, x.y, hi, lo);
+    const int oj = off + tc_rowoff<C::SBO>(tc_row<RN, NBITS>(j * p));
+    *reinterpret_cast<uint32_t *>(Ahi + oj) = hi;
+    *reinterpret_cast<uint32_t *>(Alo + oj) = lo;
   }
 }
 
-// DFT_16 of the lane's two butterflies on the tensor cores.  x[r][c]: row
-// r (0: butterfly g, 1: g + 8), point c (0..3 -> 2t, 2t+1, 2t+8, 2t+9);
-// replaced by the outputs at the same (row, index) positions.
-template <int PREC>
-__device__ __forceinline__ void tc_dft16(float2 (&x)[2][4], const uint32_t *__restrict__ fr,
-                                         int lane) {
-  uint32_t ah[2][4], al[2][4];  // [kt: 0 = real parts, 1 = imaginary parts][a-reg]
-#pragma unroll
-  for (int kt = 0; kt < 2; ++kt) {
-    auto comp = [&](const float2 &v) { return kt == 0 ? v.x : v.y; };
-    split2<PREC>(comp(x[0][0]), comp(x[0][1]), ah[kt][0], al[kt][0]);  // row g,   cols 2t..
-    split2<PREC>(comp(x[1][0]), comp(x[1][1]), ah[kt][1], al[kt][1]);  // row g+8, cols 2t..
-    split2<PREC>(comp(x[0][2]), comp(x[0][3]), ah[kt][2], al[kt][2]);  // row g,   cols 2t+8..
-    split2<PREC>(comp(x[1][2]), comp(x[1][3]), ah[kt][3], al[kt][3]);  // row g+8, cols 2t+8..
-  }
-  float acc[4][4];
-#pragma unroll
-  for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-    for (int r = 0; r < 4; ++r) acc[nt][r] = 0.f;
-#pragma unroll
-  for (int kt = 0; kt < 2; ++kt) {
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-      const uint2 bh = *reinterpret_cast<const uint2 *>(fr + (((0 * 2 + kt) * 4 + nt) * 32 + lane) * 2);
-      const uint2 bl = *reinterpret_cast<const uint2 *>(fr + (((1 * 2 + kt) * 4 + nt) * 32 + lane) * 2);
-      mma16816<PREC>(acc[nt], ah[kt], bh.x, bh.y);
-      mma16816<PREC>(acc[nt], ah[kt], bl.x, bl.y);
-      mma16816<PREC>(acc[nt], al[kt], bh.x, bh.y);
-    }
-  }
-  // accumulator (row g / g+8, cols nt*8 + 2t + {0,1}); cols 0..15 real, 16..31 imag
-#pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    x[r][0] = make_float2(acc[0][2 * r + 0], acc[2][2 * r + 0]);
-    x[r][1] = make_float2(acc[0][2 * r + 1], acc[2][2 * r + 1]);
-    x[r][2] = make_float2(acc[1][2 * r + 0], acc[3][2 * r + 0]);
-    x[r][3] = make_float2(acc[1][2 * r + 1], acc[3][2 * r + 1]);
-  }
-}
-
-__device__ __forceinline__ int tc_point(int t, int c) { return 2 * t + (c & 1) + (c >> 1) * 8; }
-
-// Shared-memory layout of the exchange after TC stage e: bit b (b < 4) of a
-// position is XOR-ed with bit src[e][b] (>= 4, or none), a permutation within
-// each 16-point block.  The source bits were chosen (by exhaustive search on a
-// model of the lane -> (butterfly, point) map) so that the half-warp accesses
-// of the writing stage and of the reading stage (TC gather or radix-4 tail)
-// hit at most 2 accesses per bank pair; the direct layout gives 4.
-__host__ __device__ constexpr int tc_src(int N, int e, int b) {
-  // rows: exchange e; columns: target bit b = 0..3
-  return N == 256     ? (e == 0 ? (b == 0 ? 4 : b == 1 ? -1 : b == 2 ? 6 : 5) : -1)
-         : N == 4096  ? (e == 0   ? (b == 0 ? 4 : b == 1 ? -1 : b == 2 ? 9 : 5)
-                         : e == 1 ? (b == 2 ? 5 : b == 3 ? 9 : -1)
-                                  : -1)
-         : N == 16384 ? (e == 0   ? (b == 0 ? 4 : b == 1 ? -1 : b == 2 ? 11 : 5)
-                         : e == 1 ? (b == 2 ? 5 : b == 3 ? 11 : -1)
-                         : e == 2 ? (b == 2 ? 9 : b == 3 ? 10 : -1)
-                                  : -1)
-                      : -1;
-}
-
-template <int N>
-__device__ __forceinline__ int tc_swz(int pos, int e) {
-  int a = 0;
-#pragma unroll
-  for (int b = 0; b < 4; ++b) {
-    const int sb = tc_src(N, e, b);
-    if (sb >= 0) a |= ((pos >> sb) & 1) << b;
-  }
-  return pos ^ a;
-}
-
-// N = 16^S (S TC stages) or 16^S * 4 (radix-4 tail).  WPR warps per row, TB
-// rows per CTA, G groups of 16 butterflies per warp per stage.
-template <int N, int D, int PREC, int S, int TAIL, int WPR, int TB, int G>
-__global__ void __launch_bounds__(TB *WPR * 32)
+template <int N, int D, int PREC>
+__global__ void __launch_bounds__(TcCfg<N>::NW * 32, TcCfg<N>::MINB)
 tc_kernel(TcArgs a) {
-  constexpr int NB = N / 16;          // butterflies per TC stage
-  static_assert(NB == WPR * G * 16, "groups must cover the stage");
-  constexpr int RT = WPR * 32;        // threads per row
-  extern __shared__ __align__(16) float2 smem[];
-  __shared__ uint32_t fr[2 * 2 * 4 * 32 * 2];  // this direction's B fragments
-  for (int i = threadIdx.x; i < 2 * 2 * 4 * 32 * 2; i += blockDim.x) fr[i] = __ldg(a.frag + i);
-  const int rb = threadIdx.x / RT;     // row slot in the CTA
-  const int rt = threadIdx.x - rb * RT;
-  const int warp = rt / 32, lane = rt & 31;
-  const int g = lane >> 2, t = lane & 3;
-  float2 *buf = smem + (size_t)rb * N;
-  const long long row = (long long)blockIdx.x * TB + rb;
-  const bool active = row < a.batch;
-  const float2 *src = a.in + row * N;
-  float2 x[G][2][4];
-  __syncthreads();  // fragments staged
-  const float2 *tw = a.tw;
-  int p = 1;
+  using C = TcCfg<N>;
+  constexpr int NB = N / 16, IB = ilog2(NB), ROWS = C::TB * NB, NBITS = ilog2(ROWS);
+  constexpr int TM = ROWS / 128, NT = C::NW * 32, TPT = TM * 4 / C::NW;
+  constexpr int PLANE = (ROWS / 8) * C::SBO;
+  constexpr uint32_t NCOL = TM * 32 <= 32 ? 32 : TM * 32;  // power of two for TM in {1, 2, 8}
+  static_assert(TM * 4 % C::NW == 0 && C::NW % 4 == 0, "warps must cover the TMEM lanes");
+  static_assert(ROWS % NT == 0, "loader threads must cover the rows");
+  extern __shared__ __align__(1024) uint8_t sm[];
+  uint8_t *Ahi = sm, *Alo = sm + PLANE, *Bs = sm + 2 * PLANE;
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + 2 * PLANE + 4096);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long row0 = (long long)blockIdx.x * C::TB;
+
+  for (int e = tid; e < 256; e += NT) reinterpret_cast<uint4 *>(Bs)[e] = __ldg(a.bimg + e);
+  if (tid == 0) {
+    mbar_init(mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(NCOL));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  // Stage 0 operand: lanes load consecutive butterflies (coalesced) and each
+  // writes its butterfly's whole row (four 16-byte chunks per plane).
 #pragma unroll
-  for (int s = 0; s < S; ++s) {
-    // gather: butterfly i = i0 + g + 8 r, point j = tc_point(t, c): input i + j NB
+  for (int q = 0; q < ROWS / NT; ++q) {
+    const int v = tid + NT * q;
+    const int b = v >> IB, i = v & (NB - 1);
+    const long long grow = row0 + b;
+    const bool active = grow < a.batch;
+    const float2 *src = a.in + grow * N + i;
+    float2 x[16];
 #pragma unroll
-    for (int q = 0; q < G; ++q) {
-      const int i0 = (warp * G + q) * 16;
+    for (int j = 0; j < 16; ++j) x[j] = active ? __ldcs(src + j * NB) : make_float2(0.f, 0.f);
+    const int ro = tc_rowoff<C::SBO>(tc_row<C::R0, NBITS>(v));
 #pragma unroll
-      for (int r = 0; r < 2; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int idx = i0 + g + 8 * r + tc_point(t, c) * NB;
-          if (s == 0) x[q][r][c] = active ? __ldcs(src + idx) : make_float2(0.f, 0.f);
-          else x[q][r][c] = buf[tc_swz<N>(idx, s - 1)];
-        }
+    for (int c = 0; c < 4; ++c) {
+      uint4 h, l;
+      split2<PREC>(x[4 * c + 0].x, x[4 * c + 0].y, h.x, l.x);
+      split2<PREC>(x[4 * c + 1].x, x[4 * c + 1].y, h.y, l.y);
+      split2<PREC>(x[4 * c + 2].x, x[4 * c + 2].y, h.z, l.z);
+      split2<PREC>(x[4 * c + 3].x, x[4 * c + 3].y, h.w, l.w);
+      *reinterpret_cast<uint4 *>(Ahi + ro + c * C::LBO) = h;
+      *reinterpret_cast<uint4 *>(Alo + ro + c * C::LBO) = l;
     }
-    if (s > 0) __syncthreads();  // every read of the buffer is done
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+  const int q4 = warp & 3, g = warp >> 2;
+  bool ok = true;
 #pragma unroll
-    for (int q = 0; q < G; ++q) {
-      const int i0 = (warp * G + q) * 16;
-      if (s > 0) {
+  for (int s = 0; s < C::S; ++s) {
+    if (tid == 0) {
+      const uint32_t idesc = tc_idesc<PREC>();
+      const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bs),
+                     bl = smem_u32(Bs + 2048);
+#pragma unroll 1
+      for (int t = 0; t < TM; ++t) {
+        const uint32_t d = tbase + 32 * t;
+        const uint32_t arow = 16 * t * C::SBO;
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-          const int k = (i0 + g + 8 * r) & (p - 1);
+        for (int pr = 0; pr < 3; ++pr) {
+          const uint32_t A = (pr == 2 ? al : ah) + arow, B = pr == 1 ? bl : bh;
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const int j = tc_point(t, c);
-            if (j) x[q][r][c] = cmul_dir<D>(x[q][r][c], __ldg(tw + (j - 1) * p + k));
+          for (int kk = 0; kk < 2; ++kk)
+            tc_mma(d, tc_desc(A + kk * 2 * C::LBO, C::LBO, C::SBO),
+                   tc_desc(B + kk * 256, 128, 512), idesc, (pr | kk) ? 1u : 0u);
+        }
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(mbar))
+          : "memory");
+    }
+    ok = __syncthreads_and(ok && mbar_wait(mbar, (unsigned)(s & 1)));
+    if (!ok) break;
+    tc_fence_after();
+    if (s + 1 < C::S) {
+#pragma unroll 1
+      for (int t = 0; t < TPT; ++t) {
+        const int tile = g + (C::NW / 4) * t;
+        const int m = 128 * tile + 32 * q4 + lane;
+        uint32_t r[32];
+        tc_ld32(tbase + ((uint32_t)(32 * q4) << 16) + 32 * tile, r);
+        tc_wait_ld();
+        if (s == 0) tc_exchange<N, D, PREC, 0>(r, m, Ahi, Alo, a.tw);
+        else tc_exchange<N, D, PREC, (C::S > 2 ? 1 : 0)>(r, m, Ahi, Alo, a.tw);
+      }
+      fence_proxy_async();
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+    } else if constexpr (C::TAIL == 0) {
+      // last stage: butterfly i (< N / 16 = its stride) writes outputs i + j N/16
+      constexpr unsigned long long RL = tc_rcode<C>(C::S - 1);
+#pragma unroll 1
+      for (int t = 0; t < TPT; ++t) {
+        const int tile = g + (C::NW / 4) * t;
+        const int m = 128 * tile + 32 * q4 + lane;
+        uint32_t r[32];
+        tc_ld32(tbase + ((uint32_t)(32 * q4) << 16) + 32 * tile, r);
+        tc_wait_ld();
+        const int v = tc_unrow<RL, NBITS>(m);
+        const int b = v >> IB, i = v & (NB - 1);
+        const long long grow = row0 + b;
+        if (grow < a.batch) {
+          float2 *dst = a.out + grow * N + i;
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            __stcs(dst + j * NB, cscale(make_float2(__uint_as_float(r[2 * j]),
+                                                    __uint_as_float(r[2 * j + 1])),
+                                        a.scale));
+        }
+      }
+    } else {
+      // radix-4 tail (stride 4096): this thread's tiles g + 2v (v = 0..3)
+      // hold butterflies k + 256 v of the last TC stage (identity rows), whose
+      // outputs j are the four points of radix-4 butterfly 256 j + k.
+      static_assert(N == 16384 && TPT == 4 && C::NW == 8, "tail mapping");
+      const int k = 128 * g + 32 * q4 + lane;
+      const long long grow = row0;
+      const bool active = grow < a.batch;
+      const float2 *tw3 = a.tw + tc_twoff(3);
+#pragma unroll 1
+      for (int jc = 0; jc < 4; ++jc) {
+        uint32_t r[4][8];
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          tc_ld8(tbase + ((uint32_t)(32 * q4) << 16) + 32 * (g + 2 * v) + 8 * jc, r[v]);
+        tc_wait_ld();
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          const int it = 256 * (4 * jc + jj) + k;
+          float2 w[4];
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            w[v] = make_float2(__uint_as_float(r[v][2 * jj]), __uint_as_float(r[v][2 * jj + 1]));
+#pragma unroll
+          for (int v = 1; v < 4; ++v) w[v] = cmul_dir<D>(w[v], __ldg(tw3 + (v - 1) * 4096 + it));
+          Dft<4, D>::run(w);
+          if (active) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+              __stcs(a.out + grow * N + it + 4096 * v, cscale(w[v], a.scale));
           }
         }
       }
-      tc_dft16<PREC>(x[q], fr, lane);
-      const bool last = (s == S - 1) && !TAIL;
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const int i = i0 + g + 8 * r;
-        const int k = i & (p - 1);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int pos = (i - k) * 16 + k + tc_point(t, c) * p;
-          if (last) {
-            if (active) __stcs(a.out + row * N + pos, cscale(x[q][r][c], a.scale));
-          } else {
-            buf[tc_swz<N>(pos, s)] = x[q][r][c];
-          }
-        }
-      }
-    }
-    if (s > 0) tw += 15 * p;
-    p *= 16;
-    if (s + 1 < S || TAIL) __syncthreads();
-  }
-  if constexpr (TAIL == 4) {
-    // radix-4 pass on the CUDA cores: p = N / 4, butterfly i reads i + j N/4
-    constexpr int Q = (N / 4) / RT;  // butterflies per thread
-    float2 v[Q][4];
-#pragma unroll
-    for (int q = 0; q < Q; ++q)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) v[q][j] = buf[tc_swz<N>(rt + q * RT + j * (N / 4), S - 1)];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      const int k = rt + q * RT;  // i = k since i < p
-#pragma unroll
-      for (int j = 1; j < 4; ++j) v[q][j] = cmul_dir<D>(v[q][j], __ldg(tw + (j - 1) * p + k));
-      float2 w[4] = {v[q][0], v[q][1], v[q][2], v[q][3]};
-      Dft<4, D>::run(w);
-      if (active)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) __stcs(a.out + row * N + k + j * (N / 4), cscale(w[j], a.scale));
     }
   }
+  if (!ok && tid == 0) atomicCAS(a.status, 0, 6 /* FFT_ERR_TIMEOUT */);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(NCOL));
 }
 
-// B fragments of G^T for both directions, from the FP64 DFT-16 matrix:
-// frag[dir][hl][kt][nt][lane][e], e = 0..3 halves (2 u32): rows k of G^T are
-// kt*16 + 2t + {0,1} (e = 0,1) and + 8 (e = 2,3), column n = nt*8 + g.
+// G images for both directions, from the FP64 DFT-16 matrix: img[dir][plane]
+// = 32 x 32 16-bit values G[n][k] (n = 2 jo + re/im of the output, k = 2 ji +
+// re/im of the input) in the K-major layout with LBO 128, SBO 512.
 template <int PREC>
-__global__ void tc_gen_fragments(uint32_t *frag) {
-  const int lane = threadIdx.x & 31;
-  const int nt = (threadIdx.x >> 5) & 3;
-  const int kt = (threadIdx.x >> 7) & 1;
-  const int dir = (threadIdx.x >> 8) & 1;  // 0: forward, 1: inverse
-  const int g = lane >> 2, t = lane & 3;
-  const int col = nt * 8 + g;              // output component: < 16 real, else imag
-  float hv[4], lv[4];
-  for (int e = 0; e < 4; ++e) {
-    const int comp = kt * 16 + 2 * t + (e & 1) + (e >> 1) * 8;  // input component
-    const int n = comp & 15, k = col & 15;
-    // W_16^{kn} with the sign of the direction, FP64
-    double s, c;
-    sincospi((dir ? 2.0 : -2.0) * (double)((k * n) % 16) / 16.0, &s, &c);
-    // G[col][comp]: [[Fr, -Fi], [Fi, Fr]]
-    double v;
-    if (col < 16) v = (comp < 16) ? c : -s;
-    else v = (comp < 16) ? s : c;
+__global__ void tc_gen_bimg(uint16_t *img) {
+  const int n = threadIdx.x >> 5, k = threadIdx.x & 31;  // 1024 threads
+  for (int dir = 0; dir < 2; ++dir) {
+    const int jo = n >> 1, ji = k >> 1;
+    double sn, cs;
+    sincospi((dir ? 2.0 : -2.0) * (double)((jo * ji) % 16) / 16.0, &sn, &cs);
+    // out_re = Fr x_re - Fi x_im ; out_im = Fi x_re + Fr x_im
+    const double gv = (n & 1) == 0 ? ((k & 1) == 0 ? cs : -sn) : ((k & 1) == 0 ? sn : cs);
+    uint16_t h, l;
     if (PREC == FFT_PREC_FP16X2) {
-      __half h = __double2half(v);
-      hv[e] = __half2float(h);
-      lv[e] = (float)(v - (double)hv[e]);
+      const __half a = __double2half(gv);
+      const __half b = __double2half(gv - (double)__half2float(a));
+      h = *reinterpret_cast<const uint16_t *>(&a);
+      l = *reinterpret_cast<const uint16_t *>(&b);
     } else {
-      __nv_bfloat16 h = __double2bfloat16(v);
-      hv[e] = __bfloat162float(h);
-      lv[e] = (float)(v - (double)hv[e]);
+      const __nv_bfloat16 a = __double2bfloat16(gv);
+      const __nv_bfloat16 b = __double2bfloat16(gv - (double)__bfloat162float(a));
+      h = *reinterpret_cast<const uint16_t *>(&a);
+      l = *reinterpret_cast<const uint16_t *>(&b);
     }
-  }
-  for (int hl = 0; hl < 2; ++hl) {
-    const float *src = hl ? lv : hv;
-    uint32_t u0, u1, dummy;
-    split2<PREC>(src[0], src[1], u0, dummy);
-    split2<PREC>(src[2], src[3], u1, dummy);
-    uint32_t *dst = frag + (size_t)dir * 2048 + (((hl * 2 + kt) * 4 + nt) * 32 + lane) * 2;
-    dst[0] = u0;
-    dst[1] = u1;
+    const int off = ((n >> 3) * 512 + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2) / 2;
+    img[dir * 2048 + off] = h;
+    img[dir * 2048 + 1024 + off] = l;
   }
 }
 
 struct TcState {
-  uint32_t *d_frag = nullptr;
+  uint16_t *d_bimg = nullptr;
   const void *fn = nullptr;
   int threads = 0, tb = 0;
   size_t smem = 0;
 };
 
-template <int N, int PREC, int S, int TAIL, int WPR, int TB, int G>
+template <int N, int PREC>
 static void pick(TcState *st, int dir) {
-  st->fn = dir < 0 ? (const void *)&tc_kernel<N, -1, PREC, S, TAIL, WPR, TB, G>
-                   : (const void *)&tc_kernel<N, +1, PREC, S, TAIL, WPR, TB, G>;
-  st->threads = TB * WPR * 32;
-  st->tb = TB;
-  st->smem = sizeof(float2) * (size_t)N * TB;
+  st->fn = dir < 0 ? (const void *)&tc_kernel<N, -1, PREC> : (const void *)&tc_kernel<N, +1, PREC>;
+  st->threads = TcCfg<N>::NW * 32;
+  st->tb = TcCfg<N>::TB;
+  st->smem = (size_t)tc_smem_bytes<N>();
 }
 
 template <int PREC>
 static bool pick_prec(TcState *st, int N, int dir) {
   switch (N) {
-    case 256: pick<256, PREC, 2, 0, 1, 8, 1>(st, dir); return true;
-    case 4096: pick<4096, PREC, 3, 0, 16, 1, 1>(st, dir); return true;
-    case 16384: pick<16384, PREC, 3, 4, 16, 1, 4>(st, dir); return true;
+    case 256: pick<256, PREC>(st, dir); return true;
+    case 4096: pick<4096, PREC>(st, dir); return true;
+    case 16384: pick<16384, PREC>(st, dir); return true;
   }
   return false;
 }
@@ -322,12 +441,12 @@ fft_status_t tc_plan(fft_plan_impl *pl) {
   TcState *st = new (std::nothrow) TcState;
   if (!st) return FFT_ERR_ALLOC;
   pl->tc = st;
-  const bool ok = pl->precision == FFT_PREC_FP16X2 ? pick_prec<FFT_PREC_FP16X2>(st, pl->N, pl->direction)
-                                                  : pick_prec<FFT_PREC_BF16X2>(st, pl->N, pl->direction);
+  const bool ok = pl->precision == FFT_PREC_FP16X2
+                      ? pick_prec<FFT_PREC_FP16X2>(st, pl->N, pl->direction)
+                      : pick_prec<FFT_PREC_BF16X2>(st, pl->N, pl->direction);
   if (!ok) return FFT_ERR_NOT_SUPPORTED;
-  if (st->smem > 48 * 1024 &&
-      cudaFuncSetAttribute(st->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st->smem) !=
-          cudaSuccess)
+  if (cudaFuncSetAttribute(st->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st->smem) !=
+      cudaSuccess)
     return FFT_ERR_CUDA;
   // twiddle tables: schedule 16, 16[, 16][, 4]
   KernelEntry k{};
@@ -337,12 +456,12 @@ fft_status_t tc_plan(fft_plan_impl *pl) {
   int64_t off = 0;
   fft_status_t s = build_twiddles(pl, pass_segments(k, off));
   if (s != FFT_OK) return s;
-  if (cudaMalloc(&st->d_frag, 2 * 2048 * sizeof(uint32_t)) != cudaSuccess) {
+  if (cudaMalloc(&st->d_bimg, 2 * 4096) != cudaSuccess) {
     cudaGetLastError();
     return FFT_ERR_ALLOC;
   }
-  if (pl->precision == FFT_PREC_FP16X2) tc_gen_fragments<FFT_PREC_FP16X2><<<1, 512>>>(st->d_frag);
-  else tc_gen_fragments<FFT_PREC_BF16X2><<<1, 512>>>(st->d_frag);
+  if (pl->precision == FFT_PREC_FP16X2) tc_gen_bimg<FFT_PREC_FP16X2><<<1, 1024>>>(st->d_bimg);
+  else tc_gen_bimg<FFT_PREC_BF16X2><<<1, 1024>>>(st->d_bimg);
   if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
     return FFT_ERR_CUDA;
   pl->path = FFT_PATH_TENSORCORE;
@@ -358,7 +477,8 @@ fft_status_t tc_exec(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t r
   a.in = in;
   a.out = out;
   a.tw = pl->d_tw;
-  a.frag = st->d_frag + (pl->direction > 0 ? 2048 : 0);
+  a.bimg = reinterpret_cast<const uint4 *>(st->d_bimg + (pl->direction > 0 ? 2048 : 0));
+  a.status = pl->d_status;
   a.batch = rows;
   a.scale = pl->scale;
   const int64_t grid = (rows + st->tb - 1) / st->tb;
@@ -370,7 +490,7 @@ fft_status_t tc_exec(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t r
 
 void tc_destroy(fft_plan_impl *pl) {
   TcState *st = (TcState *)pl->tc;
-  if (st) cudaFree(st->d_frag);
+  if (st) cudaFree(st->d_bimg);
   delete st;
   pl->tc = nullptr;
 }
