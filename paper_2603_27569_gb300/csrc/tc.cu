@@ -35,6 +35,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <new>
 
 #include "plan.h"
@@ -53,7 +54,10 @@ struct TcArgs {
   float scale;
 };
 
-// Per-size plan (MINB: CTAs per SM the register budget is sized for).
+// Per-size plan: NW warps per CTA, MINB CTAs per SM the register budget is
+// sized for, PERSIST: a resident grid walks the row groups (otherwise one
+// group per CTA, which measured faster where several CTAs share an SM: their
+// phases stay staggered).
 // Row permutations rho_s are nibble-packed: nibble b = the
 // bit of the packed butterfly index (row-in-CTA << log2 NB | butterfly) that
 // becomes bit b of the A row at stage s.
@@ -61,17 +65,20 @@ template <int N>
 struct TcCfg;
 template <>
 struct TcCfg<256> {
-  static constexpr int S = 2, TAIL = 0, TB = 16, NW = 8, LBO = 144, SBO = 576, MINB = 3;
+  static constexpr int S = 2, TAIL = 0, TB = 16, NW = 4, LBO = 144, SBO = 576, MINB = 5;
+  static constexpr bool PERSIST = false;
   static constexpr unsigned long long R0 = 0x45763021ull, R1 = 0x73526140ull, R2 = 0;
 };
 template <>
 struct TcCfg<4096> {
-  static constexpr int S = 3, TAIL = 0, TB = 1, NW = 8, LBO = 144, SBO = 576, MINB = 3;
+  static constexpr int S = 3, TAIL = 0, TB = 1, NW = 4, LBO = 144, SBO = 576, MINB = 5;
+  static constexpr bool PERSIST = false;
   static constexpr unsigned long long R0 = 0x76354210ull, R1 = 0x73210654ull, R2 = 0x76543102ull;
 };
 template <>
 struct TcCfg<16384> {
   static constexpr int S = 3, TAIL = 4, TB = 1, NW = 8, LBO = 144, SBO = 592, MINB = 1;
+  static constexpr bool PERSIST = true;
   static constexpr unsigned long long R0 = 0x8539064712ull, R1 = 0x4130576289ull,
                                       R2 = 0x9876543210ull;
 };
@@ -102,13 +109,6 @@ __host__ __device__ constexpr int tc_rowoff(int m) {
 
 // Twiddle-table offset of pass s (s >= 1) of the schedule 16, 16, 16, 4.
 __host__ __device__ constexpr int tc_twoff(int s) { return s == 1 ? 0 : s == 2 ? 240 : 4080; }
-
-// Shared-memory bytes of the kernel for size N: A hi and lo planes, the G
-// image, the mbarrier and the TMEM address slot.
-template <int N>
-__host__ __device__ constexpr int tc_smem_bytes() {
-  return 2 * (TcCfg<N>::TB * (N / 16) / 8) * TcCfg<N>::SBO + 4096 + 16;
-}
 
 // 16-bit split of (v0, v1): hi = round(v), lo = round(v - hi), packed two per u32.
 template <int PREC>
@@ -217,22 +217,34 @@ __device__ __forceinline__ void tc_exchange(const uint32_t (&r)[32], int m, uint
   }
 }
 
+// Shared-memory layout of the kernel: A hi and lo planes, the G image, the
+// MMA-completion mbarrier and the TMEM address slot.
+template <int N>
+struct TcSmem {
+  static constexpr int PLANE = (TcCfg<N>::TB * (N / 16) / 8) * TcCfg<N>::SBO;
+  static constexpr int B = 2 * PLANE, BAR = B + 4096, TOTAL = BAR + 16;
+  static_assert(B % 1024 == 0, "operand alignment");
+};
+
+// A CTA transforms groups of TB rows: one group, or (PERSIST) every
+// gridDim.x-th group from blockIdx.x.
 template <int N, int D, int PREC>
 __global__ void __launch_bounds__(TcCfg<N>::NW * 32, TcCfg<N>::MINB)
 tc_kernel(TcArgs a) {
   using C = TcCfg<N>;
+  using L = TcSmem<N>;
+  constexpr int NW = C::NW;
   constexpr int NB = N / 16, IB = ilog2(NB), ROWS = C::TB * NB, NBITS = ilog2(ROWS);
-  constexpr int TM = ROWS / 128, NT = C::NW * 32, TPT = TM * 4 / C::NW;
-  constexpr int PLANE = (ROWS / 8) * C::SBO;
+  constexpr int TM = ROWS / 128, NT = NW * 32, TPT = TM * 4 / NW;
   constexpr uint32_t NCOL = TM * 32 <= 32 ? 32 : TM * 32;  // power of two for TM in {1, 2, 8}
-  static_assert(TM * 4 % C::NW == 0 && C::NW % 4 == 0, "warps must cover the TMEM lanes");
+  static_assert(TM * 4 % NW == 0 && NW % 4 == 0, "warps must cover the TMEM lanes");
   static_assert(ROWS % NT == 0, "loader threads must cover the rows");
   extern __shared__ __align__(1024) uint8_t sm[];
-  uint8_t *Ahi = sm, *Alo = sm + PLANE, *Bs = sm + 2 * PLANE;
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + 2 * PLANE + 4096);
+  uint8_t *Ahi = sm, *Alo = sm + L::PLANE, *Bs = sm + L::B;
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + L::BAR);
   uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const long long row0 = (long long)blockIdx.x * C::TB;
+  const long long ngroups = (a.batch + C::TB - 1) / C::TB;
 
   for (int e = tid; e < 256; e += NT) reinterpret_cast<uint4 *>(Bs)[e] = __ldg(a.bimg + e);
   if (tid == 0) {
@@ -245,135 +257,143 @@ tc_kernel(TcArgs a) {
                  "r"(NCOL));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  // Stage 0 operand: lanes load consecutive butterflies (coalesced) and each
-  // writes its butterfly's whole row (four 16-byte chunks per plane).
-#pragma unroll
-  for (int q = 0; q < ROWS / NT; ++q) {
-    const int v = tid + NT * q;
-    const int b = v >> IB, i = v & (NB - 1);
-    const long long grow = row0 + b;
-    const bool active = grow < a.batch;
-    const float2 *src = a.in + grow * N + i;
-    float2 x[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) x[j] = active ? __ldcs(src + j * NB) : make_float2(0.f, 0.f);
-    const int ro = tc_rowoff<C::SBO>(tc_row<C::R0, NBITS>(v));
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      uint4 h, l;
-      split2<PREC>(x[4 * c + 0].x, x[4 * c + 0].y, h.x, l.x);
-      split2<PREC>(x[4 * c + 1].x, x[4 * c + 1].y, h.y, l.y);
-      split2<PREC>(x[4 * c + 2].x, x[4 * c + 2].y, h.z, l.z);
-      split2<PREC>(x[4 * c + 3].x, x[4 * c + 3].y, h.w, l.w);
-      *reinterpret_cast<uint4 *>(Ahi + ro + c * C::LBO) = h;
-      *reinterpret_cast<uint4 *>(Alo + ro + c * C::LBO) = l;
-    }
-  }
-  fence_proxy_async();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tslot;
-  const int q4 = warp & 3, g = warp >> 2;
+  const int q4 = warp & 3, g4 = warp >> 2;
   bool ok = true;
+  unsigned mph = 0;  // completed phases of the MMA mbarrier
+  for (long long grp = blockIdx.x; grp < ngroups; grp += C::PERSIST ? gridDim.x : ngroups) {
+    const long long row0 = grp * C::TB;
+    // Stage 0 operand: lanes take consecutive butterflies and each writes its
+    // butterfly's whole row (four 16-byte chunks per plane).
 #pragma unroll
-  for (int s = 0; s < C::S; ++s) {
-    if (tid == 0) {
-      const uint32_t idesc = tc_idesc<PREC>();
-      const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bs),
-                     bl = smem_u32(Bs + 2048);
-#pragma unroll 1
-      for (int t = 0; t < TM; ++t) {
-        const uint32_t d = tbase + 32 * t;
-        const uint32_t arow = 16 * t * C::SBO;
-#pragma unroll
-        for (int pr = 0; pr < 3; ++pr) {
-          const uint32_t A = (pr == 2 ? al : ah) + arow, B = pr == 1 ? bl : bh;
-#pragma unroll
-          for (int kk = 0; kk < 2; ++kk)
-            tc_mma(d, tc_desc(A + kk * 2 * C::LBO, C::LBO, C::SBO),
-                   tc_desc(B + kk * 256, 128, 512), idesc, (pr | kk) ? 1u : 0u);
-        }
-      }
-      asm volatile(
-          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              smem_u32(mbar))
-          : "memory");
-    }
-    ok = __syncthreads_and(ok && mbar_wait(mbar, (unsigned)(s & 1)));
-    if (!ok) break;
-    tc_fence_after();
-    if (s + 1 < C::S) {
-#pragma unroll 1
-      for (int t = 0; t < TPT; ++t) {
-        const int tile = g + (C::NW / 4) * t;
-        const int m = 128 * tile + 32 * q4 + lane;
-        uint32_t r[32];
-        tc_ld32(tbase + ((uint32_t)(32 * q4) << 16) + 32 * tile, r);
-        tc_wait_ld();
-        if (s == 0) tc_exchange<N, D, PREC, 0>(r, m, Ahi, Alo, a.tw);
-        else tc_exchange<N, D, PREC, (C::S > 2 ? 1 : 0)>(r, m, Ahi, Alo, a.tw);
-      }
-      fence_proxy_async();
-      tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-    } else if constexpr (C::TAIL == 0) {
-      // last stage: butterfly i (< N / 16 = its stride) writes outputs i + j N/16
-      constexpr unsigned long long RL = tc_rcode<C>(C::S - 1);
-#pragma unroll 1
-      for (int t = 0; t < TPT; ++t) {
-        const int tile = g + (C::NW / 4) * t;
-        const int m = 128 * tile + 32 * q4 + lane;
-        uint32_t r[32];
-        tc_ld32(tbase + ((uint32_t)(32 * q4) << 16) + 32 * tile, r);
-        tc_wait_ld();
-        const int v = tc_unrow<RL, NBITS>(m);
-        const int b = v >> IB, i = v & (NB - 1);
-        const long long grow = row0 + b;
-        if (grow < a.batch) {
-          float2 *dst = a.out + grow * N + i;
-#pragma unroll
-          for (int j = 0; j < 16; ++j)
-            __stcs(dst + j * NB, cscale(make_float2(__uint_as_float(r[2 * j]),
-                                                    __uint_as_float(r[2 * j + 1])),
-                                        a.scale));
-        }
-      }
-    } else {
-      // radix-4 tail (stride 4096): this thread's tiles g + 2v (v = 0..3)
-      // hold butterflies k + 256 v of the last TC stage (identity rows), whose
-      // outputs j are the four points of radix-4 butterfly 256 j + k.
-      static_assert(N == 16384 && TPT == 4 && C::NW == 8, "tail mapping");
-      const int k = 128 * g + 32 * q4 + lane;
-      const long long grow = row0;
+    for (int q = 0; q < ROWS / NT; ++q) {
+      const int v = tid + NT * q;
+      const int b = v >> IB, i = v & (NB - 1);
+      const long long grow = row0 + b;
       const bool active = grow < a.batch;
-      const float2 *tw3 = a.tw + tc_twoff(3);
+      const float2 *src = a.in + grow * N + i;
+      float2 x[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) x[j] = active ? __ldcs(src + j * NB) : make_float2(0.f, 0.f);
+      const int ro = tc_rowoff<C::SBO>(tc_row<C::R0, NBITS>(v));
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        uint4 h, l;
+        split2<PREC>(x[4 * c + 0].x, x[4 * c + 0].y, h.x, l.x);
+        split2<PREC>(x[4 * c + 1].x, x[4 * c + 1].y, h.y, l.y);
+        split2<PREC>(x[4 * c + 2].x, x[4 * c + 2].y, h.z, l.z);
+        split2<PREC>(x[4 * c + 3].x, x[4 * c + 3].y, h.w, l.w);
+        *reinterpret_cast<uint4 *>(Ahi + ro + c * C::LBO) = h;
+        *reinterpret_cast<uint4 *>(Alo + ro + c * C::LBO) = l;
+      }
+    }
+    fence_proxy_async();  // A for the tensor core
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+#pragma unroll
+    for (int s = 0; s < C::S; ++s) {
+      if (tid == 0) {
+        const uint32_t idesc = tc_idesc<PREC>();
+        const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bs),
+                       bl = smem_u32(Bs + 2048);
 #pragma unroll 1
-      for (int jc = 0; jc < 4; ++jc) {
-        uint32_t r[4][8];
+        for (int t = 0; t < TM; ++t) {
+          const uint32_t d = tbase + 32 * t;
+          const uint32_t arow = 16 * t * C::SBO;
 #pragma unroll
-        for (int v = 0; v < 4; ++v)
-          tc_ld8(tbase + ((uint32_t)(32 * q4) << 16) + 32 * (g + 2 * v) + 8 * jc, r[v]);
-        tc_wait_ld();
+          for (int pr = 0; pr < 3; ++pr) {
+            const uint32_t A = (pr == 2 ? al : ah) + arow, B = pr == 1 ? bl : bh;
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-          const int it = 256 * (4 * jc + jj) + k;
-          float2 w[4];
+            for (int kk = 0; kk < 2; ++kk)
+              tc_mma(d, tc_desc(A + kk * 2 * C::LBO, C::LBO, C::SBO),
+                     tc_desc(B + kk * 256, 128, 512), idesc, (pr | kk) ? 1u : 0u);
+          }
+        }
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(mbar))
+            : "memory");
+      }
+      ok = __syncthreads_and(ok && mbar_wait(mbar, mph & 1));
+      if (!ok) break;
+      ++mph;
+      tc_fence_after();
+      if (s + 1 < C::S) {
+#pragma unroll 1
+        for (int t = 0; t < TPT; ++t) {
+          const int tile = g4 + (NW / 4) * t;
+          const int m = 128 * tile + 32 * q4 + lane;
+          uint32_t r[32];
+          tc_ld32(tbase + ((uint32_t)(32 * q4) << 16) + 32 * tile, r);
+          tc_wait_ld();
+          if (s == 0) tc_exchange<N, D, PREC, 0>(r, m, Ahi, Alo, a.tw);
+          else tc_exchange<N, D, PREC, (C::S > 2 ? 1 : 0)>(r, m, Ahi, Alo, a.tw);
+        }
+        fence_proxy_async();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+      } else if constexpr (C::TAIL == 0) {
+        // last stage: butterfly i (< N / 16 = its stride) writes outputs i + j N/16
+        constexpr unsigned long long RL = tc_rcode<C>(C::S - 1);
+#pragma unroll 1
+        for (int t = 0; t < TPT; ++t) {
+          const int tile = g4 + (NW / 4) * t;
+          const int m = 128 * tile + 32 * q4 + lane;
+          uint32_t r[32];
+          tc_ld32(tbase + ((uint32_t)(32 * q4) << 16) + 32 * tile, r);
+          tc_wait_ld();
+          const int v = tc_unrow<RL, NBITS>(m);
+          const int b = v >> IB, i = v & (NB - 1);
+          const long long grow = row0 + b;
+          if (grow < a.batch) {
+            float2 *dst = a.out + grow * N + i;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              __stcs(dst + j * NB, cscale(make_float2(__uint_as_float(r[2 * j]),
+                                                      __uint_as_float(r[2 * j + 1])),
+                                          a.scale));
+          }
+        }
+      } else {
+        // radix-4 tail (stride 4096): this thread's tiles g + 2v (v = 0..3)
+        // hold butterflies k + 256 v of the last TC stage (identity rows),
+        // whose outputs j are the four points of radix-4 butterfly 256 j + k.
+        static_assert(N == 16384 && TPT == 4 && NW == 8, "tail mapping");
+        const int k = 128 * g4 + 32 * q4 + lane;
+        const float2 *tw3 = a.tw + tc_twoff(3);
+#pragma unroll 1
+        for (int jc = 0; jc < 4; ++jc) {
+          uint32_t r[4][8];
 #pragma unroll
           for (int v = 0; v < 4; ++v)
-            w[v] = make_float2(__uint_as_float(r[v][2 * jj]), __uint_as_float(r[v][2 * jj + 1]));
+            tc_ld8(tbase + ((uint32_t)(32 * q4) << 16) + 32 * (g4 + 2 * v) + 8 * jc, r[v]);
+          tc_wait_ld();
 #pragma unroll
-          for (int v = 1; v < 4; ++v) w[v] = cmul_dir<D>(w[v], __ldg(tw3 + (v - 1) * 4096 + it));
-          Dft<4, D>::run(w);
-          if (active) {
+          for (int jj = 0; jj < 4; ++jj) {
+            const int it = 256 * (4 * jc + jj) + k;
+            float2 w[4];
 #pragma unroll
             for (int v = 0; v < 4; ++v)
-              __stcs(a.out + grow * N + it + 4096 * v, cscale(w[v], a.scale));
+              w[v] = make_float2(__uint_as_float(r[v][2 * jj]), __uint_as_float(r[v][2 * jj + 1]));
+#pragma unroll
+            for (int v = 1; v < 4; ++v)
+              w[v] = cmul_dir<D>(w[v], __ldg(tw3 + (v - 1) * 4096 + it));
+            Dft<4, D>::run(w);
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+              __stcs(a.out + row0 * N + it + 4096 * v, cscale(w[v], a.scale));
           }
         }
       }
     }
+    if (!ok) break;
+    // (the next group's first MMA is issued after its stage-0 barrier, which
+    // every thread reaches after its last TMEM read of this group)
   }
   if (!ok && tid == 0) atomicCAS(a.status, 0, 6 /* FFT_ERR_TIMEOUT */);
   tc_fence_before();
@@ -417,6 +437,8 @@ struct TcState {
   const void *fn = nullptr;
   int threads = 0, tb = 0;
   size_t smem = 0;
+  bool persist = false;
+  int64_t grid_cap = 0;  // CTAs per launch: occupancy x SMs when persistent
 };
 
 template <int N, int PREC>
@@ -424,7 +446,8 @@ static void pick(TcState *st, int dir) {
   st->fn = dir < 0 ? (const void *)&tc_kernel<N, -1, PREC> : (const void *)&tc_kernel<N, +1, PREC>;
   st->threads = TcCfg<N>::NW * 32;
   st->tb = TcCfg<N>::TB;
-  st->smem = (size_t)tc_smem_bytes<N>();
+  st->smem = (size_t)TcSmem<N>::TOTAL;
+  st->persist = TcCfg<N>::PERSIST;
 }
 
 template <int PREC>
@@ -448,6 +471,13 @@ fft_status_t tc_plan(fft_plan_impl *pl) {
   if (cudaFuncSetAttribute(st->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st->smem) !=
       cudaSuccess)
     return FFT_ERR_CUDA;
+  int dev = 0, sms = 0, occ = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, st->fn, st->threads, st->smem) !=
+          cudaSuccess || occ < 1)
+    return FFT_ERR_CUDA;
+  st->grid_cap = st->persist ? (int64_t)occ * sms : 0x7fffffffLL;
   // twiddle tables: schedule 16, 16[, 16][, 4]
   KernelEntry k{};
   k.npass = pl->N == 256 ? 2 : pl->N == 4096 ? 3 : 4;
@@ -481,8 +511,9 @@ fft_status_t tc_exec(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t r
   a.status = pl->d_status;
   a.batch = rows;
   a.scale = pl->scale;
-  const int64_t grid = (rows + st->tb - 1) / st->tb;
-  if (grid > 0x7fffffffLL) return FFT_ERR_INVALID_SIZE;
+  const int64_t groups = (rows + st->tb - 1) / st->tb;
+  if (!st->persist && groups > st->grid_cap) return FFT_ERR_INVALID_SIZE;
+  const int64_t grid = std::min<int64_t>(groups, st->grid_cap);
   void *args[] = {&a};
   return cuda_status(
       cudaLaunchKernel(st->fn, dim3((unsigned)grid), dim3(st->threads), args, st->smem, stream));
