@@ -362,6 +362,7 @@ def run_ours(args):
         extras["ragged"] = bench_ragged(fg, synth, torch, dev)
         extras["tensorcore"] = bench_tc(fg, synth, torch, dev)
         extras["fp16_storage"] = bench_fp16_storage(fg, torch, dev, per_key_ms)
+        extras["large_n"] = bench_large_n(fg, torch, dev)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nthreads = os.cpu_count() or 1
@@ -517,6 +518,34 @@ def bench_fp16_storage(fg, torch, dev, per_key_ms):
                        "gflops": round(flops(N, POINTS // N) / (ms * 1e-3) / 1e9, 1),
                        "frac_hbm": round(8.0 * POINTS / (ms * 1e-3) / 1e9 / peaks()[0], 4),
                        "speedup_vs_fp32": round(per_key_ms[(N, fg.FFT_FORWARD)] / ms, 3)}
+    return out
+
+
+def bench_large_n(fg, torch, dev):
+    """N = 2^15..2^20 (beyond one CTA: the two-phase four-step), 2^25 points
+    per call, forward, default plan (split chosen by the planner)."""
+    out = {}
+    x = torch.randn(POINTS, dtype=torch.complex64, device=dev)
+    y = torch.empty_like(x)
+    for e in range(15, 21):
+        N = 1 << e
+        p = fg.Plan(N, POINTS // N, fg.FFT_FORWARD, device=dev)
+        for _ in range(3):
+            p(x, out=y)
+        torch.cuda.synchronize()
+        reps = 10
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            p(x, out=y)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        info = p.info()
+        p.close()
+        out[str(N)] = {"us": round(ms * 1e3, 2), "n1": info["n1"], "n2": info["n2"],
+                       "gflops": round(flops(N, POINTS // N) / (ms * 1e-3) / 1e9, 1),
+                       "frac_hbm": round(16.0 * POINTS / (ms * 1e-3) / 1e9 / peaks()[0], 4)}
     return out
 
 

@@ -137,9 +137,10 @@ const char *fft_status_string(fft_status_t status);
 
 /*
  * fft_plan — plan `batch` transforms of length N in one direction.
- * N: power of two, 2 <= N <= 65536.  Up to 16384 a row fits one CTA; above
- * that only the two-phase four-step runs (N = n1 * n2, n1, n2 <= 256; its
- * intermediate doubles the HBM traffic).  batch >= 0 (0 makes a valid plan whose
+ * N: power of two, 2 <= N <= 2^20.  Up to 16384 a row fits one CTA; above
+ * that only the two-phase four-step runs (N = n1 * n2 with a phase-1 length
+ * n2 <= 256 and a phase-2 length n1 <= 4096; its intermediate doubles the
+ * HBM traffic).  batch >= 0 (0 makes a valid plan whose
  * exec does nothing).  direction: FFT_FORWARD or FFT_INVERSE.
  * Allocates and fills the plan's twiddle tables on the current device
  * (generated in FP64 on the GPU, rounded to FP32) and synchronises once.

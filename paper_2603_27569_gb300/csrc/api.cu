@@ -368,20 +368,22 @@ static int64_t elem_bytes(const fft_plan_impl *pl) {
 }
 
 // Largest N: single CTA (the whole row in registers + shared memory), and
-// overall (two-phase four-step with both factors <= 256).
+// overall (two-phase four-step: phase 1 <= 256 points, phase 2 <= 4096).
 constexpr int kMaxSingleN = 16384;
-constexpr int kMaxN = 65536;
+constexpr int kMaxN = 1 << 20;
 
 // Built-in launch shape of the single-CTA path: one CTA per tile (measured
 // faster than the persistent shape for every N up to 8192 on GB300; the
 // staged kernels used at N = 16384 are persistent by construction).
 constexpr int kDefaultCtasPerSm = 0;
 
-// Four-step split N = n1 * n2 with both factors column-kernel lengths (16..256).
+// Four-step split N = n1 * n2: n2 (phase 1) a length with a twiddle +
+// transposed-store column kernel (16..256), n1 (phase 2) a length with a
+// plain column kernel (16..4096).
 static bool fourstep_split(int N, int want_n1, int *n1, int *n2) {
   auto ok = [&](int a) {
-    int b = N / a;
-    return a >= 16 && b >= 16 && a <= 256 && b <= 256 && default_column(b, 1) && default_column(a, 0);
+    const int b = N / a;
+    return a >= 16 && b >= 16 && default_column(b, 1) && default_column(a, 0);
   };
   if (want_n1 > 0) {
     if (N % want_n1 || !ok(want_n1)) return false;
@@ -389,10 +391,13 @@ static bool fourstep_split(int N, int want_n1, int *n1, int *n2) {
     *n2 = N / want_n1;
     return true;
   }
-  // Prefer n2 >= n1 (longer first-phase transforms), as square as possible.
+  // Prefer n2 >= n1 (longer first-phase transforms), as square as possible;
+  // beyond 256 x 256, phase 1 stays at 256 points and phase 2 grows.
   int best = 0;
-  for (int a = 16; a <= 256; a *= 2)
+  for (int a = 16; a <= 4096 && a <= N; a *= 2)
     if (N % a == 0 && ok(a) && a <= N / a) best = a;
+  for (int a = 16; !best && a <= 4096 && a <= N; a *= 2)
+    if (N % a == 0 && ok(a)) best = a;
   if (!best) return false;
   *n1 = best;
   *n2 = N / best;
@@ -724,7 +729,7 @@ int fft_list_configs(int N, fft_config_t *out, int capacity) {
     c.tma_slabs = e.slabs;
     emit(c);
   }
-  for (int a = 16; a <= 256; a *= 2) {
+  for (int a = 16; a <= 4096 && a <= N; a *= 2) {
     int n1, n2;
     if (N % a || !fourstep_split(N, a, &n1, &n2)) continue;
     const KernelEntry *k = default_column(n2, 1);

@@ -9,8 +9,9 @@
 //            X[k2 + N2 k1].
 //
 // Both phases read C consecutive columns of every row, so each warp load
-// covers whole 128-byte segments.  In shared memory element (row, c) of the
-// tile sits at row * C + c: a half-warp always touches 16 consecutive
+// covers whole row segments (128 bytes at C = 16; 32 bytes, one sector, at
+// the narrowest C = 4).  In shared memory element (row, c) of the tile sits
+// at row * C + c: with C = 16 a half-warp always touches 16 consecutive
 // columns, so every exchange is free of bank conflicts without a swizzle.
 // Phase 1 stores its result transposed (column-major) through a padded
 // shared tile so that the global store is coalesced as well.

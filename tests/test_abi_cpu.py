@@ -67,7 +67,7 @@ def _plan_ex(L, N, batch, direction, prec=0, flags=0):
     return rc, h.value
 
 
-@pytest.mark.parametrize("N", [0, 1, 3, 12, 100, 131072, 1 << 20])
+@pytest.mark.parametrize("N", [0, 1, 3, 12, 100, 3 << 16, 1 << 21, 1 << 24])
 def test_plan_rejects_bad_sizes(L, N):
     rc, h = _plan_ex(L, N, 4, -1)
     assert rc == INVALID_SIZE and h is None
@@ -116,10 +116,14 @@ def test_configs_listed_for_every_supported_size(L):
             else:
                 assert prod == N // c["n1"] and N % c["n1"] == 0
     assert fg.fft_list_configs(12) == []
-    assert fg.fft_list_configs(131072) == []
-    for N in (32768, 65536):   # beyond one CTA: two-phase four-step only
+    assert fg.fft_list_configs(1 << 21) == []
+    for e in range(15, 21):   # beyond one CTA: two-phase four-step only
+        N = 1 << e
         cfgs = fg.fft_list_configs(N)
         assert cfgs and all(c["path"] == fg.FFT_PATH_FOURSTEP for c in cfgs)
+        for c in cfgs:
+            n2 = N // c["n1"]
+            assert c["n1"] * n2 == N and 16 <= n2 <= 256 and c["n1"] <= 4096
     for N in (8192, 16384):
         assert any(c["path"] == fg.FFT_PATH_FOURSTEP for c in fg.fft_list_configs(N))
 

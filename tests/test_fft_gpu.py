@@ -270,11 +270,18 @@ def test_host_buffer_exec_matches_device_exec(N, flags):
     check(x[:4], host[:4], fg.FFT_FORWARD)
 
 
-@pytest.mark.parametrize("N", [32768, 65536])
+@pytest.mark.parametrize("N", [1 << e for e in range(15, 21)])
 @pytest.mark.parametrize("direction", [fg.FFT_FORWARD, fg.FFT_INVERSE])
 def test_beyond_one_cta_fourstep(N, direction):
-    # N > 16384: the two-phase four-step (n1, n2 <= 256) is the only path
+    # N > 16384: the two-phase four-step (phase 1 <= 256 points, phase 2 <=
+    # 4096) is the only path; every listed split, ragged CTA tail included
+    cfgs = fg.fft_list_configs(N)
+    assert cfgs
     x = synth.gaussian((3, N), seed=N)
     y, info = run(x, direction)
     assert info["path"] == fg.FFT_PATH_FOURSTEP and info["n1"] * info["n2"] == N
     check(x, y, direction)
+    for cfg in cfgs:
+        y, info = run(x[:2], direction, config=cfg)
+        assert info["n1"] == cfg["n1"]
+        check(x[:2], y, direction)
