@@ -125,10 +125,10 @@ __global__ void gen_pass_twiddles(float2 *out, int p, int r) {
   out[idx] = make_float2(__double2float_rn(c), __double2float_rn(s));
 }
 
-// Full table: entry e = W_M^e, 0 <= e < M.
-__global__ void gen_full_twiddles(float2 *out, int64_t M) {
+// Full table: entry e = W_M^e, 0 <= e < count (count <= M).
+__global__ void gen_full_twiddles(float2 *out, int64_t M, int64_t count) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= M) return;
+  if (e >= count) return;
   double s, c;
   sincospi(-2.0 * (double)e / (double)M, &s, &c);
   out[e] = make_float2(__double2float_rn(c), __double2float_rn(s));
@@ -169,7 +169,7 @@ fft_status_t build_twiddles(fft_plan_impl *pl, const std::vector<TwSeg> &segs) {
     if (g.kind == 0)
       gen_pass_twiddles<<<blocks, threads>>>(pl->d_tw + g.offset, g.p, g.r);
     else
-      gen_full_twiddles<<<blocks, threads>>>(pl->d_tw + g.offset, g.M);
+      gen_full_twiddles<<<blocks, threads>>>(pl->d_tw + g.offset, g.M, g.count);
     FFTGB_CUDA(cudaGetLastError());
   }
   FFTGB_CUDA(cudaDeviceSynchronize());

@@ -30,7 +30,7 @@ namespace fftgb {
 
 // Twiddle generators of the regular planner (api.cu), reused unchanged.
 __global__ void gen_pass_twiddles(float2 *out, int p, int r);
-__global__ void gen_full_twiddles(float2 *out, int64_t M);
+__global__ void gen_full_twiddles(float2 *out, int64_t M, int64_t count);
 
 namespace {
 
@@ -110,7 +110,7 @@ fft_status_t setup_device(int dev, DeviceSetup **out) {
       z.tw2 = off;
       off = fill_pass_tables(z.k2, d.tw, off);
       z.twbig = off;
-      gen_full_twiddles<<<(unsigned)((N + 255) / 256), 256>>>(d.tw + off, N);
+      gen_full_twiddles<<<(unsigned)((N + 255) / 256), 256>>>(d.tw + off, N, N);
       off += N;
       if (off > kTwEntries) return FFT_ERR_NOT_SUPPORTED;
     }
