@@ -246,9 +246,12 @@ def run_ours(args):
     # Autotune every (N, direction) on this GPU before anything is timed: the
     # plans below then use the fastest compiled configuration.
     if not args.no_autotune:
-        for N in SIZES:
-            for d in (fg.FFT_FORWARD, fg.FFT_INVERSE):
-                fg.fft_autotune(N, d, 0, POINTS // N)
+        if args.autotune_cache and os.path.exists(args.autotune_cache):
+            fg.fft_autotune_load(args.autotune_cache)      # choices of an earlier run
+        else:
+            for N in SIZES:
+                for d in (fg.FFT_FORWARD, fg.FFT_INVERSE):
+                    fg.fft_autotune(N, d, 0, POINTS // N, args.autotune_cache or None)
 
     # Inputs: one 2^25-point N(0,1) buffer (seed 0), viewed as [2^25/N, N].
     x = torch.from_numpy(synth.gaussian(POINTS, seed=0)).to(dev)
@@ -661,6 +664,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune-cache", type=str, default="",
+                    help="load the autotuner's choices from this JSON if it exists, "
+                         "else tune and write them there")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the built-in configurations instead of autotuning first")
     ap.add_argument("--profile-case", type=int, default=0,
