@@ -48,6 +48,7 @@ struct TcArgs {
   const float2 *in;
   float2 *out;
   const float2 *tw;       // pass tables of the schedule 16, 16[, 16][, 4]
+  const float2 *twx;      // exchange twiddles in TMEM-row order: [stage][j][row]
   const uint4 *bimg;      // this direction's G image: hi plane, lo plane (2 KiB each)
   int *status;            // FFT_ERR_TIMEOUT if an MMA completion wait ran out
   long long batch;
@@ -191,7 +192,7 @@ __device__ __forceinline__ void tc_wait_ld() {
 // offset plus a compile-time constant per j.
 template <int N, int D, int PREC, int s>
 __device__ __forceinline__ void tc_exchange(const uint32_t (&r)[32], int m, uint8_t *Ahi,
-                                            uint8_t *Alo, const float2 *__restrict__ tw) {
+                                            uint8_t *Alo, const float2 *__restrict__ twx) {
   using C = TcCfg<N>;
   constexpr int NB = N / 16, IB = ilog2(NB), NBITS = ilog2(C::TB * NB);
   constexpr int p = s == 0 ? 1 : s == 1 ? 16 : 256, LP = 4 * s;
@@ -204,11 +205,15 @@ __device__ __forceinline__ void tc_exchange(const uint32_t (&r)[32], int m, uint
   const int j2 = base >> IB;                  // the next stage's point index
   const int m2 = tc_row<RN, NBITS>((b << IB) | (base & (NB - 1)));
   const int off = tc_rowoff<C::SBO>(m2) + (j2 >> 2) * C::LBO + (j2 & 3) * 4;
-  const float2 *twp = tw + tc_twoff(s + 1) + (j2 > 0 ? (j2 - 1) * 16 * p : 0) + k;
+  // The next pass's twiddle W_{256 p}^{j2 (j p + k)} of this row's output j,
+  // from a table laid out [stage][j][row]: a warp's 32 rows read 256
+  // contiguous bytes per j.
+  constexpr int ROWS = C::TB * NB;
+  const float2 *twp = twx + (s * 16) * ROWS + m;
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
     float2 x = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
-    if (j2 > 0) x = cmul_dir<D>(x, __ldg(twp + j * p));
+    x = cmul_dir<D>(x, __ldg(twp + j * ROWS));
     uint32_t hi, lo;
     split2<PREC>(x.x, x.y, hi, lo);
     const int oj = off + tc_rowoff<C::SBO>(tc_row<RN, NBITS>(j * p));
@@ -330,8 +335,8 @@ tc_kernel(TcArgs a) {
           uint32_t r[32];
           tc_ld32(tbase + ((uint32_t)(32 * q4) << 16) + 32 * tile, r);
           tc_wait_ld();
-          if (s == 0) tc_exchange<N, D, PREC, 0>(r, m, Ahi, Alo, a.tw);
-          else tc_exchange<N, D, PREC, (C::S > 2 ? 1 : 0)>(r, m, Ahi, Alo, a.tw);
+          if (s == 0) tc_exchange<N, D, PREC, 0>(r, m, Ahi, Alo, a.twx);
+          else tc_exchange<N, D, PREC, (C::S > 2 ? 1 : 0)>(r, m, Ahi, Alo, a.twx);
         }
         fence_proxy_async();
         tc_fence_before();
@@ -432,17 +437,49 @@ __global__ void tc_gen_bimg(uint16_t *img) {
   }
 }
 
+// Exchange twiddles in TMEM-row order: out[(s * 16 + j) * ROWS + m] = the
+// twiddle that output j of the butterfly in row m of stage s takes into stage
+// s + 1, W_{256 p}^{j2 (j p + k)} (p = 16^s; butterfly i = p u + k, j2 = its
+// next point index), forward sign (the kernels conjugate for the inverse),
+// from the exact integer exponent in FP64, rounded to FP32.
+template <int N>
+__global__ void tc_gen_twx(float2 *out) {
+  using C = TcCfg<N>;
+  constexpr int NB = N / 16, IB = ilog2(NB), ROWS = C::TB * NB, NBITS = ilog2(ROWS);
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (C::S - 1) * 16 * ROWS) return;
+  const int s = idx / (16 * ROWS), j = (idx / ROWS) % 16, m = idx % ROWS;
+  const int v = s == 0 ? tc_unrow<C::R0, NBITS>(m) : tc_unrow<C::R1, NBITS>(m);
+  const int p = s == 0 ? 1 : 16, LP = 4 * s;
+  const int i = v & (NB - 1), k = i & (p - 1), u = i >> LP;
+  const int j2 = ((u << (LP + 4)) | k) >> IB;
+  const long long M = 256LL * p, e = ((long long)j2 * (j * p + k)) % M;
+  double sn, cs;
+  sincospi(-2.0 * (double)e / (double)M, &sn, &cs);
+  out[idx] = make_float2(__double2float_rn(cs), __double2float_rn(sn));
+}
+
 struct TcState {
-  uint16_t *d_bimg = nullptr;
+  uint16_t *d_bimg = nullptr;  // G images, both directions (8 KiB)
+  float2 *d_twx = nullptr;     // exchange twiddles in TMEM-row order
   const void *fn = nullptr;
   int threads = 0, tb = 0;
   size_t smem = 0;
   bool persist = false;
+  int64_t twx_count = 0;
+  const void *gen_twx = nullptr;
   int64_t grid_cap = 0;  // CTAs per launch: occupancy x SMs when persistent
 };
 
+template <int N>
+static int64_t twx_count() {
+  return (int64_t)(TcCfg<N>::S - 1) * 16 * TcCfg<N>::TB * (N / 16);
+}
+
 template <int N, int PREC>
 static void pick(TcState *st, int dir) {
+  st->twx_count = twx_count<N>();
+  st->gen_twx = (const void *)&tc_gen_twx<N>;
   st->fn = dir < 0 ? (const void *)&tc_kernel<N, -1, PREC> : (const void *)&tc_kernel<N, +1, PREC>;
   st->threads = TcCfg<N>::NW * 32;
   st->tb = TcCfg<N>::TB;
@@ -486,12 +523,19 @@ fft_status_t tc_plan(fft_plan_impl *pl) {
   int64_t off = 0;
   fft_status_t s = build_twiddles(pl, pass_segments(k, off));
   if (s != FFT_OK) return s;
-  if (cudaMalloc(&st->d_bimg, 2 * 4096) != cudaSuccess) {
+  if (cudaMalloc(&st->d_bimg, 2 * 4096) != cudaSuccess ||
+      cudaMalloc(&st->d_twx, sizeof(float2) * (size_t)st->twx_count) != cudaSuccess) {
     cudaGetLastError();
     return FFT_ERR_ALLOC;
   }
   if (pl->precision == FFT_PREC_FP16X2) tc_gen_bimg<FFT_PREC_FP16X2><<<1, 1024>>>(st->d_bimg);
   else tc_gen_bimg<FFT_PREC_BF16X2><<<1, 1024>>>(st->d_bimg);
+  {
+    void *args[] = {&st->d_twx};
+    const unsigned blocks = (unsigned)((st->twx_count + 255) / 256);
+    if (cudaLaunchKernel(st->gen_twx, dim3(blocks), dim3(256), args, 0, 0) != cudaSuccess)
+      return FFT_ERR_CUDA;
+  }
   if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
     return FFT_ERR_CUDA;
   pl->path = FFT_PATH_TENSORCORE;
@@ -508,6 +552,7 @@ fft_status_t tc_exec(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t r
   a.out = out;
   a.tw = pl->d_tw;
   a.bimg = reinterpret_cast<const uint4 *>(st->d_bimg + (pl->direction > 0 ? 2048 : 0));
+  a.twx = st->d_twx;
   a.status = pl->d_status;
   a.batch = rows;
   a.scale = pl->scale;
@@ -521,7 +566,10 @@ fft_status_t tc_exec(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t r
 
 void tc_destroy(fft_plan_impl *pl) {
   TcState *st = (TcState *)pl->tc;
-  if (st) cudaFree(st->d_bimg);
+  if (st) {
+    cudaFree(st->d_bimg);
+    cudaFree(st->d_twx);
+  }
   delete st;
   pl->tc = nullptr;
 }
