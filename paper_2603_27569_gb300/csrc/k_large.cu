@@ -6,4 +6,4 @@
 FFTGB_STOCKHAM(8192, 16, 1, 0, 16, 16, 16, 2);
 FFTGB_STOCKHAM(8192, 32, 1, 2, 32, 16, 16);
 FFTGB_STOCKHAM(16384, 16, 1, 0, 16, 16, 16, 4);
-FFTGB_STOCKHAM(16384, 32, 1, 0, 32, 32, 16);
+FFTGB_STOCKHAM(16384, 32, 1, 2, 32, 32, 16);

@@ -4,6 +4,6 @@
 #include "instantiate.cuh"
 
 FFTGB_STAGED(16384, 16, 12, 0, 16, 16, 16, 4);
-FFTGB_STAGED(16384, 32, 24, 2, 32, 32, 16);
+FFTGB_STAGED(16384, 32, 24, 0, 32, 32, 16);
 FFTGB_STAGED(8192, 16, 16, 0, 16, 16, 16, 2);
 FFTGB_STAGED(8192, 32, 32, 0, 32, 16, 16);

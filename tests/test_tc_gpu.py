@@ -68,3 +68,31 @@ def test_unsupported_sizes_are_refused():
     with pytest.raises(fg.FFTError) as e:
         fg.Plan(1024, 4, fg.FFT_FORWARD, precision=fg.FFT_PREC_FP16X2)
     assert e.value.status == 7
+
+
+@pytest.mark.parametrize("N", [256, 4096, 16384])
+@pytest.mark.parametrize("batch", [1, 17])
+def test_small_and_ragged_batches(N, batch):
+    # one row; and (N = 256, 16 rows per CTA) a partly filled last row group
+    x = synth.gaussian((batch, N), seed=batch)
+    y = run_tc(x, fg.FFT_FORWARD, "fp16x2")
+    err = rel_l2_rows(y, oracle.fft(x, nthreads=NTHREADS))
+    assert err.max() <= TOL_SPLIT
+
+
+@pytest.mark.parametrize("N", [256, 4096, 16384])
+def test_in_place_round_trip_and_determinism(N):
+    x = synth.gaussian((9, N), seed=11)
+    fwd = fg.Plan(N, 9, fg.FFT_FORWARD, precision=fg.FFT_PREC_FP16X2)
+    inv = fg.Plan(N, 9, fg.FFT_INVERSE, precision=fg.FFT_PREC_FP16X2)
+    xd = to_dev(x)
+    a = to_host(fwd(xd))
+    b = to_host(fwd(xd))
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))   # run-to-run bitwise
+    fwd(xd, out=xd)                                                 # in place
+    assert np.array_equal(to_host(xd).view(np.uint32), a.view(np.uint32))
+    back = to_host(inv(xd))
+    fwd.close()
+    inv.close()
+    assert rel_l2_rows(back, x).max() <= 2 * TOL_SPLIT
+    assert np.isfinite(back).all()
