@@ -365,6 +365,8 @@ def run_ours(args):
         extras["ragged"] = bench_ragged(fg, synth, torch, dev)
         extras["tensorcore"] = bench_tc(fg, synth, torch, dev)
         extras["fp16_storage"] = bench_fp16_storage(fg, torch, dev, per_key_ms)
+        extras["bf16_storage"] = bench_fp16_storage(fg, torch, dev, per_key_ms,
+                                                    fg.FFT_PREC_BF16_STORAGE)
         extras["large_n"] = bench_large_n(fg, torch, dev)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -496,15 +498,20 @@ def bench_tc(fg, synth, torch, dev):
     return out
 
 
-def bench_fp16_storage(fg, torch, dev, per_key_ms):
-    """FP16-storage transforms (4 bytes per point in HBM, FP32 arithmetic) over
-    the sweep's sizes, 2^25 points per call, forward; vs the FP32 plan."""
+def bench_fp16_storage(fg, torch, dev, per_key_ms, precision=None):
+    """16-bit-storage transforms (FP16 pairs, or BF16 pairs as interleaved
+    torch.bfloat16; 4 bytes per point in HBM, FP32 arithmetic) over the sweep's
+    sizes, 2^25 points per call, forward; vs the FP32 plan."""
+    precision = fg.FFT_PREC_FP16_STORAGE if precision is None else precision
     out = {}
-    x = torch.randn(POINTS, dtype=torch.complex64, device=dev).to(torch.complex32)
+    x = torch.randn(POINTS, dtype=torch.complex64, device=dev)
+    if precision == fg.FFT_PREC_BF16_STORAGE:
+        x = torch.view_as_real(x).to(torch.bfloat16).reshape(-1)
+    else:
+        x = x.to(torch.complex32)
     y = torch.empty_like(x)
     for N in SIZES:
-        p = fg.Plan(N, POINTS // N, fg.FFT_FORWARD, precision=fg.FFT_PREC_FP16_STORAGE,
-                    device=dev)
+        p = fg.Plan(N, POINTS // N, fg.FFT_FORWARD, precision=precision, device=dev)
         for _ in range(3):
             p(x, out=y)
         torch.cuda.synchronize()

@@ -48,10 +48,14 @@ typedef enum {
     FFT_PREC_FP32 = 0,    /* FP32 data and arithmetic (the plain path)        */
     FFT_PREC_FP16X2 = 1,  /* tensor-core radix-16 DFT, FP16 hi+lo operands     */
     FFT_PREC_BF16X2 = 2,  /* tensor-core radix-16 DFT, BF16 hi+lo operands     */
-    FFT_PREC_FP16_STORAGE = 3 /* data in HBM as FP16 (re, im) pairs, 4 bytes per
+    FFT_PREC_FP16_STORAGE = 3, /* data in HBM as FP16 (re, im) pairs, 4 bytes per
                                point; FP32 arithmetic; output rounded to FP16
                                (overflow to infinity: the caller keeps
                                |X| below 65504).  N in [256, 16384].          */
+    FFT_PREC_BF16_STORAGE = 4  /* data in HBM as BF16 (re, im) pairs, 4 bytes per
+                               point; FP32 arithmetic; output rounded to BF16
+                               (FP32 range, 8 significant bits).
+                               N in [256, 16384].                             */
 } fft_precision_t;
 
 typedef enum {
@@ -179,7 +183,8 @@ fft_status_t fft_plan_config(fft_plan_t *out, int N, int64_t batch, int directio
 /*
  * fft_exec — run the plan on device buffers.
  * in, out: device pointers to batch*N float2 each (see layout above; batch*N
- * FP16 pairs, 4 bytes each, for FFT_PREC_FP16_STORAGE), 16-byte
+ * FP16 or BF16 pairs, 4 bytes each, for FFT_PREC_FP16_STORAGE or
+ * FFT_PREC_BF16_STORAGE), 16-byte
  * aligned; in == out is allowed, partial overlap is FFT_ERR_INVALID_VALUE.
  * For a ragged plan, in and out are the packed base pointers the plan's
  * offsets index.  stream: cudaStream_t or NULL.  Asynchronous.

@@ -14,7 +14,7 @@ import threading
 
 __all__ = [
     "FFTError", "FFT_FORWARD", "FFT_INVERSE", "FFT_PREC_FP32", "FFT_PREC_FP16X2",
-    "FFT_PREC_BF16X2", "FFT_PREC_FP16_STORAGE", "FFT_FLAG_UNNORMALIZED_INVERSE", "FFT_FLAG_FORCE_SINGLE_CTA",
+    "FFT_PREC_BF16X2", "FFT_PREC_FP16_STORAGE", "FFT_PREC_BF16_STORAGE", "FFT_FLAG_UNNORMALIZED_INVERSE", "FFT_FLAG_FORCE_SINGLE_CTA",
     "FFT_FLAG_FORCE_FOURSTEP", "FFT_FLAG_NO_AUTOTUNE_CACHE", "FFT_FLAG_ADJOINT",
     "FFT_PATH_SINGLE_CTA", "FFT_PATH_FOURSTEP", "FFT_PATH_RAGGED", "FFT_PATH_TENSORCORE",
     "STATUS", "lib", "library_path", "fft_status_string", "fft_plan", "fft_plan_ex", "fft_exec",
@@ -30,6 +30,7 @@ __all__ = [
 FFT_FORWARD = -1
 FFT_INVERSE = 1
 FFT_PREC_FP32, FFT_PREC_FP16X2, FFT_PREC_BF16X2, FFT_PREC_FP16_STORAGE = 0, 1, 2, 3
+FFT_PREC_BF16_STORAGE = 4
 FFT_FLAG_UNNORMALIZED_INVERSE = 0x1
 FFT_FLAG_FORCE_SINGLE_CTA = 0x2
 FFT_FLAG_FORCE_FOURSTEP = 0x4

@@ -304,8 +304,8 @@ fft_status_t exec_rows(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t
   }
   if (pl->path == FFT_PATH_SINGLE_CTA && pl->k_single->kind == KIND_HALFIO) {
     HalfArgs a;
-    a.in = (const __half2 *)in;
-    a.out = (__half2 *)out;
+    a.in = in;    // FP16 or BF16 pairs, per the kernel's variant
+    a.out = out;
     a.tw = pl->d_tw + pl->tw_single;
     a.batch = rows;
     a.scale = pl->scale;
@@ -364,7 +364,9 @@ static bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 
 // Bytes per stored point: 8 (complex64), 4 for FP16 storage.
 static int64_t elem_bytes(const fft_plan_impl *pl) {
-  return pl->precision == FFT_PREC_FP16_STORAGE ? 4 : (int64_t)sizeof(float2);
+  return (pl->precision == FFT_PREC_FP16_STORAGE || pl->precision == FFT_PREC_BF16_STORAGE)
+             ? 4
+             : (int64_t)sizeof(float2);
 }
 
 // Largest N: single CTA (the whole row in registers + shared memory), and
@@ -562,7 +564,7 @@ static fft_status_t plan_common(fft_plan_t *out, int N, int64_t batch, int direc
   *out = nullptr;
   if (!is_pow2(N) || N < 2 || N > kMaxN || batch < 0) return FFT_ERR_INVALID_SIZE;
   if (direction != FFT_FORWARD && direction != FFT_INVERSE) return FFT_ERR_INVALID_VALUE;
-  if (precision < FFT_PREC_FP32 || precision > FFT_PREC_FP16_STORAGE) return FFT_ERR_INVALID_VALUE;
+  if (precision < FFT_PREC_FP32 || precision > FFT_PREC_BF16_STORAGE) return FFT_ERR_INVALID_VALUE;
   if (flags & ~(FFT_FLAG_UNNORMALIZED_INVERSE | FFT_FLAG_FORCE_SINGLE_CTA |
                 FFT_FLAG_FORCE_FOURSTEP | FFT_FLAG_NO_AUTOTUNE_CACHE | FFT_FLAG_ADJOINT))
     return FFT_ERR_INVALID_VALUE;
@@ -624,10 +626,11 @@ static fft_status_t plan_common(fft_plan_t *out, int N, int64_t batch, int direc
       } else {
         s = FFT_ERR_INVALID_VALUE;
       }
-    } else if (precision == FFT_PREC_FP16_STORAGE) {
+    } else if (precision == FFT_PREC_FP16_STORAGE || precision == FFT_PREC_BF16_STORAGE) {
+      const int variant = precision == FFT_PREC_BF16_STORAGE ? 1 : 0;
       const KernelEntry *k = nullptr;
       for (const auto &e : kernel_registry())
-        if (e.kind == KIND_HALFIO && e.N == N) k = &e;
+        if (e.kind == KIND_HALFIO && e.N == N && e.variant == variant) k = &e;
       s = k ? plan_single(pl, k, 0) : FFT_ERR_NOT_SUPPORTED;
     } else if (precision != FFT_PREC_FP32) {
       s = tc_plan(pl);

@@ -1,5 +1,7 @@
 // Helpers that instantiate a kernel configuration and register it.
 #pragma once
+#include <type_traits>
+
 #include "cluster.cuh"
 #include "column.cuh"
 #include "fourstep_l2.cuh"
@@ -71,7 +73,7 @@ inline KernelEntry split2_entry() {
   return e;
 }
 
-template <int N, int P, int TB, int TWM, class SC>
+template <int N, int P, int TB, int TWM, class SC, class S2>
 inline KernelEntry half_entry() {
   KernelEntry e{};
   e.kind = KIND_HALFIO;
@@ -83,8 +85,9 @@ inline KernelEntry half_entry() {
   fill_radix<SC>(e);
   e.is_default = 1;
   e.twm = TWM;
-  e.fn[0] = (const void *)&stockham_half_kernel<N, P, TB, -1, SC, TWM>;
-  e.fn[1] = (const void *)&stockham_half_kernel<N, P, TB, +1, SC, TWM>;
+  e.variant = std::is_same<S2, __nv_bfloat162>::value ? 1 : 0;  // 0 FP16, 1 BF16 pairs
+  e.fn[0] = (const void *)&stockham_half_kernel<N, P, TB, -1, SC, TWM, S2>;
+  e.fn[1] = (const void *)&stockham_half_kernel<N, P, TB, +1, SC, TWM, S2>;
   return e;
 }
 
@@ -148,10 +151,13 @@ inline KernelEntry fourstep_l2_entry() {
       ::fftgb::split2_entry<N, P, 0, DEF == 1, ::fftgb::Sched<__VA_ARGS__>>()); \
   static ::fftgb::Registrar FFTGB_CAT(fftgb_reg_, __COUNTER__)(              \
       ::fftgb::split2_entry<N, P, 1, DEF == 2, ::fftgb::Sched<__VA_ARGS__>>())
-// FFTGB_HALF(N, P, TB, twiddle mode, radices...): FP16-storage kernel.
+// FFTGB_HALF(N, P, TB, twiddle mode, radices...): 16-bit-storage kernels,
+// FP16 pairs (variant 0) and BF16 pairs (variant 1).
 #define FFTGB_HALF(N, P, TB, TWM, ...)                                       \
   static ::fftgb::Registrar FFTGB_CAT(fftgb_reg_, __COUNTER__)(              \
-      ::fftgb::half_entry<N, P, TB, TWM, ::fftgb::Sched<__VA_ARGS__>>())
+      ::fftgb::half_entry<N, P, TB, TWM, ::fftgb::Sched<__VA_ARGS__>, __half2>()); \
+  static ::fftgb::Registrar FFTGB_CAT(fftgb_reg_, __COUNTER__)(              \
+      ::fftgb::half_entry<N, P, TB, TWM, ::fftgb::Sched<__VA_ARGS__>, __nv_bfloat162>())
 // FFTGB_COLUMN(L, P, C, variant, is_default, radices...)
 #define FFTGB_COLUMN(L, P, C, VAR, DEF, ...)                                 \
   static ::fftgb::Registrar FFTGB_CAT(fftgb_reg_, __COUNTER__)(              \

@@ -28,7 +28,8 @@ struct KernelEntry {
   int radix[8];   // (split2: the schedule of the N/2-point half)
   int tw_total;   // entries of the per-pass twiddle tables
   int is_default; // the built-in choice for this (kind, N, variant)
-  int variant;    // column kernels: 0 plain, 1 twiddle + transposed store
+  int variant;    // column kernels: 0 plain, 1 twiddle + transposed store;
+                  // 16-bit storage: 0 FP16 pairs, 1 BF16 pairs
   int twm;        // twiddle mode: 0 all from tables, 1 rows 1/4(/16) + products
   int slabs;      // staged kernels: slabs held in the TMA ring (0 otherwise)
   const void *fn[2];  // [0] forward (D = -1), [1] inverse (D = +1)

@@ -27,19 +27,22 @@ __all__ = ["Plan", "get_plan", "fft", "ifft", "fft_host", "SpectralFilter",
            "spectral_filter", "clear_plan_cache"]
 
 _PREC = {"fp32": B.FFT_PREC_FP32, "fp16x2": B.FFT_PREC_FP16X2, "bf16x2": B.FFT_PREC_BF16X2,
-         "fp16_storage": B.FFT_PREC_FP16_STORAGE}
+         "fp16_storage": B.FFT_PREC_FP16_STORAGE, "bf16_storage": B.FFT_PREC_BF16_STORAGE}
 
 
 def _check_tensor(x: torch.Tensor, N: int, batch: int, what: str,
                   dtype=torch.complex64) -> None:
+    """Complex dtypes hold one point per element; torch.bfloat16 (BF16 pairs,
+    torch has no complex BF16 type) holds interleaved (re, im), two per point."""
     if not isinstance(x, torch.Tensor):
         raise TypeError(f"{what} must be a torch.Tensor")
     if x.dtype != dtype:
         raise TypeError(f"{what} must be {dtype}, got {x.dtype}")
     if not x.is_contiguous():
         raise ValueError(f"{what} must be contiguous")
-    if x.numel() != N * batch:
-        raise ValueError(f"{what} has {x.numel()} elements, plan needs {N * batch}")
+    per_point = 2 if dtype == torch.bfloat16 else 1
+    if x.numel() != per_point * N * batch:
+        raise ValueError(f"{what} has {x.numel()} elements, plan needs {per_point * N * batch}")
 
 
 class Plan:
@@ -62,8 +65,13 @@ class Plan:
 
     @property
     def dtype(self):
-        """complex64, or torch.complex32 (FP16 pairs) for FP16 storage."""
-        return torch.complex32 if self.precision == B.FFT_PREC_FP16_STORAGE else torch.complex64
+        """complex64; torch.complex32 (FP16 pairs) for FP16 storage; torch.bfloat16
+        with interleaved (re, im), 2 elements per point, for BF16 storage."""
+        if self.precision == B.FFT_PREC_FP16_STORAGE:
+            return torch.complex32
+        if self.precision == B.FFT_PREC_BF16_STORAGE:
+            return torch.bfloat16
+        return torch.complex64
 
     def exec(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None):
         if not x.is_cuda or x.device != self.device:
