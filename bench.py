@@ -368,6 +368,7 @@ def run_ours(args):
         extras["bf16_storage"] = bench_fp16_storage(fg, torch, dev, per_key_ms,
                                                     fg.FFT_PREC_BF16_STORAGE)
         extras["large_n"] = bench_large_n(fg, torch, dev)
+        extras["azimuth_columns"] = bench_columns(fg, torch, dev)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nthreads = os.cpu_count() or 1
@@ -528,6 +529,33 @@ def bench_fp16_storage(fg, torch, dev, per_key_ms, precision=None):
                        "gflops": round(flops(N, POINTS // N) / (ms * 1e-3) / 1e9, 1),
                        "frac_hbm": round(8.0 * POINTS / (ms * 1e-3) / 1e9 / peaks()[0], 4),
                        "speedup_vs_fp32": round(per_key_ms[(N, fg.FFT_FORWARD)] / ms, 3)}
+    return out
+
+
+def bench_columns(fg, torch, dev):
+    """Azimuth pass without a transpose: L-point transforms down the columns
+    of one contiguous [L, 2^25 / L] matrix (fft_plan_columns), forward."""
+    out = {}
+    x = torch.randn(POINTS, dtype=torch.complex64, device=dev)
+    y = torch.empty_like(x)
+    for L in (256, 1024, 4096):
+        ncols = POINTS // L
+        p = fg.ColumnPlan(L, ncols, 1, device=dev)
+        for _ in range(3):
+            p(x, y)
+        torch.cuda.synchronize()
+        reps = 10
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            p(x, y)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        p.close()
+        out[str(L)] = {"us": round(ms * 1e3, 2), "ncols": ncols,
+                       "gflops": round(flops(L, ncols) / (ms * 1e-3) / 1e9, 1),
+                       "frac_hbm": round(16.0 * POINTS / (ms * 1e-3) / 1e9 / peaks()[0], 4)}
     return out
 
 

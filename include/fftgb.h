@@ -86,6 +86,7 @@ typedef enum {
 #define FFT_PATH_RAGGED 3      /* persistent ragged launch                    */
 #define FFT_PATH_TENSORCORE 4  /* split-precision tensor-core radix-16 DFT    */
 #define FFT_PATH_FILTER 5      /* fused spectral filter (fft_filter_plan)     */
+#define FFT_PATH_COLUMNS 6     /* strided column transforms (fft_plan_columns) */
 
 /* What a plan chose; filled by fft_plan_info(). */
 typedef struct {
@@ -306,6 +307,29 @@ fft_status_t fft_filter_forward(fft_plan_t plan, const void *x, const void *H, v
 fft_status_t fft_filter_backward(fft_plan_t plan, const void *g_y, const void *H,
                                  const void *X_saved, void *grad_x, void *grad_H,
                                  void *stream);
+
+/*
+ * fft_plan_columns — transforms down the columns of strided matrices without
+ * a transpose: the azimuth pass (corner turn) of SAR processing over a
+ * [azimuth, range] matrix stored range-contiguous (paper Sec. II-D, range and
+ * azimuth compression as batched 1-D FFTs; Sec. IX-A).  Element (m, r, c) of
+ * matrix m, row r (the transform index, 0 <= r < L) and column c (0 <= c <
+ * ncols) is at complex offset m * mat_stride + r * row_stride + c from the
+ * buffer pointer, for input and output alike; each of the nmat * ncols
+ * columns gets an L-point transform (W_L = e^{-2 pi i / L}, forward
+ * unnormalised, inverse scaled by 1/L unless FFT_FLAG_UNNORMALIZED_INVERSE).
+ * L: power of two in [16, 4096].  ncols: a multiple of the kernel's column
+ * tile (16 for L <= 1024, 8 for 2048, 4 for 4096), else FFT_ERR_INVALID_SIZE.
+ * row_stride >= ncols and < 2^31; mat_stride >= (L - 1) * row_stride + ncols
+ * (matrices do not overlap); nmat >= 0 (0: exec does nothing).  Execute with
+ * fft_exec(plan, in, out, stream): device pointers, 8-byte aligned, in == out
+ * allowed, any other overlap of the two extents is FFT_ERR_INVALID_VALUE;
+ * fft_exec_host is FFT_ERR_NOT_SUPPORTED.  Each CTA reads its columns whole
+ * before writing them, so the in-place transform is safe.
+ */
+fft_status_t fft_plan_columns(fft_plan_t *out, int L, int64_t ncols, int64_t nmat,
+                              int64_t row_stride, int64_t mat_stride, int direction,
+                              int flags);
 
 /*
  * fft_fourstep_noalloc — the two-phase four-step transform (same kernels and

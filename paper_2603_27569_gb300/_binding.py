@@ -24,7 +24,7 @@ __all__ = [
     "fft_filter_grad_h_workspace", "fft_filter_grad_h", "fft_filter_plan",
     "fft_filter_forward", "fft_filter_backward", "FFT_PATH_FILTER",
     "PlanInfo", "Config", "EXPORTED_SYMBOLS", "fft_list_configs", "fft_plan_config",
-    "fft_fourstep_noalloc", "FFT_NOALLOC_MAX_POINTS",
+    "fft_fourstep_noalloc", "FFT_NOALLOC_MAX_POINTS", "fft_plan_columns", "FFT_PATH_COLUMNS",
 ]
 
 FFT_FORWARD = -1
@@ -38,6 +38,7 @@ FFT_FLAG_NO_AUTOTUNE_CACHE = 0x8
 FFT_FLAG_ADJOINT = 0x10
 FFT_PATH_SINGLE_CTA, FFT_PATH_FOURSTEP, FFT_PATH_RAGGED, FFT_PATH_TENSORCORE = 1, 2, 3, 4
 FFT_PATH_FILTER = 5
+FFT_PATH_COLUMNS = 6
 FFT_NOALLOC_MAX_POINTS = 2097152
 
 STATUS = {
@@ -128,6 +129,7 @@ _SIGS = {
     "fft_list_configs": ([_i32, _vp, _i32], _i32),
     "fft_plan_config": ([ctypes.POINTER(_vp), _i32, _i64, _i32, _i32, ctypes.POINTER(Config)], _i32),
     "fft_fourstep_noalloc": ([_vp, _vp, _i32, _i64, _i32, _vp], _i32),
+    "fft_plan_columns": ([ctypes.POINTER(_vp), _i32, _i64, _i64, _i64, _i64, _i32, _i32], _i32),
 }
 EXPORTED_SYMBOLS = tuple(_SIGS)
 
@@ -312,6 +314,15 @@ def fft_plan_config(N: int, batch: int, direction: int, config: dict, flags: int
     h = _vp()
     _check(lib().fft_plan_config(ctypes.byref(h), N, batch, direction, flags, ctypes.byref(c)),
            "fft_plan_config")
+    return h.value
+
+
+def fft_plan_columns(L: int, ncols: int, nmat: int, row_stride: int, mat_stride: int,
+                     direction: int, flags: int = 0) -> int:
+    """Plan L-point transforms down the columns of nmat strided matrices."""
+    h = _vp()
+    _check(lib().fft_plan_columns(ctypes.byref(h), L, ncols, nmat, row_stride, mat_stride,
+                                  direction, flags), "fft_plan_columns")
     return h.value
 
 

@@ -789,6 +789,32 @@ fft_status_t fft_exec(fft_plan_t plan, const void *in, void *out, void *stream) 
     return ragged_exec(pl, (const float2 *)in, (float2 *)out, (cudaStream_t)stream);
   }
   if (pl->path == FFT_PATH_FILTER) return FFT_ERR_INVALID_VALUE;  // use fft_filter_forward
+  if (pl->path == FFT_PATH_COLUMNS) {
+    if (pl->batch == 0) return FFT_OK;
+    if (!in || !out) return FFT_ERR_INVALID_VALUE;
+    if (((uintptr_t)in & 7) || ((uintptr_t)out & 7)) return FFT_ERR_MISALIGNED;
+    const int64_t extent = (int64_t)sizeof(float2) *
+                           ((pl->col_nmat - 1) * pl->col_mat_stride +
+                            (int64_t)(pl->N - 1) * pl->col_row_stride + pl->col_ncols);
+    if (in != out) {
+      const char *a = (const char *)in, *b = (const char *)out;
+      if (a < b + extent && b < a + extent) return FFT_ERR_INVALID_VALUE;
+    }
+    ColumnArgs c{};
+    c.in = (const float2 *)in;
+    c.out = (float2 *)out;
+    c.tw = pl->d_tw + pl->tw_col2;
+    c.tw_big = nullptr;
+    c.nmat = pl->col_nmat;
+    c.in_mat_stride = pl->col_mat_stride;
+    c.out_mat_stride = pl->col_mat_stride;
+    c.in_row_stride = (int)pl->col_row_stride;
+    c.out_row_stride = (int)pl->col_row_stride;
+    c.ncols = (int)pl->col_ncols;
+    c.ntot = 0;  // no four-step twiddle on this path
+    c.scale = pl->scale;
+    return launch_column(pl->k_col2, pl->direction, c, (cudaStream_t)stream);
+  }
   if (pl->batch == 0) return FFT_OK;
   fft_status_t s = check_buffers(in, out, elem_bytes(pl) * pl->N * pl->batch);
   if (s != FFT_OK) return s;
@@ -798,7 +824,8 @@ fft_status_t fft_exec(fft_plan_t plan, const void *in, void *out, void *stream) 
 fft_status_t fft_exec_host(fft_plan_t plan, const void *host_in, void *host_out, void *stream) {
   if (!plan) return FFT_ERR_INVALID_VALUE;
   fft_plan_impl *pl = &plan->impl;
-  if (pl->path == FFT_PATH_RAGGED || pl->path == FFT_PATH_FILTER) return FFT_ERR_NOT_SUPPORTED;
+  if (pl->path == FFT_PATH_RAGGED || pl->path == FFT_PATH_FILTER || pl->path == FFT_PATH_COLUMNS)
+    return FFT_ERR_NOT_SUPPORTED;
   if (pl->batch == 0) return FFT_OK;
   if (!host_in || !host_out) return FFT_ERR_INVALID_VALUE;
   cudaStream_t st = (cudaStream_t)stream;
@@ -875,6 +902,61 @@ fft_status_t fft_destroy(fft_plan_t plan) {
   return FFT_OK;
 }
 
+fft_status_t fft_plan_columns(fft_plan_t *out, int L, int64_t ncols, int64_t nmat,
+                              int64_t row_stride, int64_t mat_stride, int direction,
+                              int flags) {
+  if (!out) return FFT_ERR_INVALID_VALUE;
+  *out = nullptr;
+  if (!is_pow2(L) || L < 16 || L > 4096) return FFT_ERR_INVALID_SIZE;
+  if (direction != FFT_FORWARD && direction != FFT_INVERSE) return FFT_ERR_INVALID_VALUE;
+  if (flags & ~FFT_FLAG_UNNORMALIZED_INVERSE) return FFT_ERR_INVALID_VALUE;
+  const KernelEntry *k = default_column(L, 0);
+  if (!k) return FFT_ERR_NOT_SUPPORTED;
+  if (ncols < 0 || nmat < 0) return FFT_ERR_INVALID_SIZE;
+  if (ncols % k->TB != 0 || ncols > 0x7fffffffLL) return FFT_ERR_INVALID_SIZE;
+  if (row_stride < ncols || row_stride > 0x7fffffffLL) return FFT_ERR_INVALID_VALUE;
+  if (nmat > 1 && mat_stride < (int64_t)(L - 1) * row_stride + ncols) return FFT_ERR_INVALID_VALUE;
+  if (mat_stride < 0) return FFT_ERR_INVALID_VALUE;
+  if (nmat * (ncols / k->TB) > 0x7fffffffLL) return FFT_ERR_INVALID_SIZE;
+  fft_plan_s *h = new (std::nothrow) fft_plan_s;
+  if (!h) return FFT_ERR_ALLOC;
+  fft_plan_impl *pl = &h->impl;
+  pl->N = L;
+  pl->batch = nmat * ncols;
+  pl->direction = direction;
+  pl->flags = flags;
+  pl->scale = (direction == FFT_INVERSE && !(flags & FFT_FLAG_UNNORMALIZED_INVERSE))
+                  ? 1.0f / (float)L
+                  : 1.0f;
+  pl->path = FFT_PATH_COLUMNS;
+  pl->k_col2 = k;
+  pl->col_ncols = ncols;
+  pl->col_nmat = nmat;
+  pl->col_row_stride = row_stride;
+  pl->col_mat_stride = mat_stride;
+  cudaGetDevice(&pl->device);
+  fft_status_t s = FFT_OK;
+  if (cudaMalloc(&pl->d_status, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    s = FFT_ERR_ALLOC;
+  } else if (cudaMemset(pl->d_status, 0, sizeof(int)) != cudaSuccess) {
+    s = FFT_ERR_CUDA;
+  }
+  if (s == FFT_OK) s = ensure_smem_attr(k);
+  if (s == FFT_OK) {
+    int64_t off = 0;
+    pl->tw_col2 = 0;
+    s = build_twiddles(pl, pass_segments(*k, off));
+  }
+  if (s != FFT_OK) {
+    free_plan(pl);
+    delete h;
+    return s;
+  }
+  *out = h;
+  return FFT_OK;
+}
+
 fft_status_t fft_plan_info(fft_plan_t plan, fft_plan_info_t *info) {
   if (!plan || !info) return FFT_ERR_INVALID_VALUE;
   const fft_plan_impl *pl = &plan->impl;
@@ -887,6 +969,7 @@ fft_status_t fft_plan_info(fft_plan_t plan, fft_plan_info_t *info) {
   info->scratch_bytes = pl->scratch_bytes;
   const KernelEntry *k = pl->path == FFT_PATH_SINGLE_CTA ? pl->k_single
                          : pl->path == FFT_PATH_FOURSTEP ? (pl->k_l2 ? pl->k_l2 : pl->k_col1)
+                         : pl->path == FFT_PATH_COLUMNS  ? pl->k_col2
                                                          : nullptr;
   if (k) {
     info->points_per_thread = k->P;

@@ -38,6 +38,10 @@ struct fft_plan_impl {
   // four-step path: phase-1 and phase-2 column kernels, split N = n1 * n2
   const KernelEntry *k_col1 = nullptr, *k_col2 = nullptr;
   int n1 = 0, n2 = 0;
+  // column path (fft_plan_columns): transforms down the columns of strided
+  // matrices, element (mat, row, col) at mat * col_mat_stride + row *
+  // col_row_stride + col
+  int64_t col_ncols = 0, col_nmat = 0, col_row_stride = 0, col_mat_stride = 0;
   // four-step in one launch with the intermediate in an L2 ring (n1 == n2):
   // chunks of l2_rows rows, l2_slots ring slots, phase 2 of a chunk claimed
   // l2_lag rounds after its phase 1; d_l2cnt = the launch's work counters

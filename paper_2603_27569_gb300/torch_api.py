@@ -24,7 +24,7 @@ import torch
 from . import _binding as B
 
 __all__ = ["Plan", "get_plan", "fft", "ifft", "fft_host", "SpectralFilter",
-           "spectral_filter", "clear_plan_cache"]
+           "spectral_filter", "clear_plan_cache", "ColumnPlan", "fft_columns"]
 
 _PREC = {"fp32": B.FFT_PREC_FP32, "fp16x2": B.FFT_PREC_FP16X2, "bf16x2": B.FFT_PREC_BF16X2,
          "fp16_storage": B.FFT_PREC_FP16_STORAGE, "bf16_storage": B.FFT_PREC_BF16_STORAGE}
@@ -144,6 +144,7 @@ def get_plan(N: int, batch: int, direction: int, precision: int = 0, flags: int 
 def clear_plan_cache() -> None:
     with _cache_lock:
         _cache.clear()
+        _col_cache.clear()
 
 
 def _raw(x: torch.Tensor, direction: int, precision: int, flags: int, out=None) -> torch.Tensor:
@@ -190,6 +191,89 @@ def fft_host(x: torch.Tensor, inverse: bool = False, device=None) -> torch.Tenso
     batch = x.numel() // N
     plan = get_plan(N, batch, B.FFT_INVERSE if inverse else B.FFT_FORWARD, 0, 0, device)
     return plan.exec_host(x.contiguous()).view(x.shape)
+
+
+class ColumnPlan:
+    """L-point transforms down the columns of [nmat, L, ncols] complex64 views
+    (row and matrix strides in elements): the azimuth pass of SAR processing
+    without a transpose (C ABI: fft_plan_columns)."""
+
+    def __init__(self, L: int, ncols: int, nmat: int = 1, row_stride: int | None = None,
+                 mat_stride: int | None = None, direction: int = B.FFT_FORWARD, flags: int = 0,
+                 device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
+            else torch.device(device)
+        self.L, self.ncols, self.nmat = L, ncols, nmat
+        self.row_stride = ncols if row_stride is None else row_stride
+        self.mat_stride = L * self.row_stride if mat_stride is None else mat_stride
+        with torch.cuda.device(self.device):
+            self.handle = B.fft_plan_columns(L, ncols, nmat, self.row_stride, self.mat_stride,
+                                             direction, flags)
+
+    def _check(self, x: torch.Tensor, what: str) -> None:
+        if not isinstance(x, torch.Tensor) or x.dtype != torch.complex64:
+            raise TypeError(f"{what} must be a complex64 torch.Tensor")
+        if not x.is_cuda or x.device != self.device:
+            raise ValueError(f"{what} must live on {self.device}")
+        need = (self.nmat - 1) * self.mat_stride + (self.L - 1) * self.row_stride + self.ncols
+        if self.nmat and x.storage_offset() + need > x.untyped_storage().nbytes() // 8:
+            raise ValueError(f"{what} does not hold the planned strided extent")
+
+    def __call__(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        """x (and out): tensors whose data pointer is the first matrix's (0, 0)."""
+        self._check(x, "input")
+        if out is None:
+            out = torch.empty_like(x)
+        self._check(out, "output")
+        st = torch.cuda.current_stream(self.device) if stream is None else stream
+        B.fft_exec(self.handle, x, out, st)
+        return out
+
+    def info(self) -> dict:
+        return B.fft_plan_info(self.handle)
+
+    def close(self) -> None:
+        h, self.handle = getattr(self, "handle", None), None
+        if h:
+            try:
+                with torch.cuda.device(self.device):
+                    B.fft_destroy(h)
+            except Exception:
+                pass
+
+    def __del__(self):
+        self.close()
+
+
+def fft_columns(x: torch.Tensor, inverse: bool = False) -> torch.Tensor:
+    """Transform along dim -2 of a complex64 CUDA tensor [..., L, ncols] whose
+    last dim is contiguous (other strides are passed to the kernel as they
+    are); returns a tensor of the same shape and strides."""
+    if x.dim() < 2 or x.stride(-1) != 1:
+        raise ValueError("need [..., L, ncols] with a contiguous last dimension")
+    lead = x.shape[:-2]
+    if len(lead) > 1:
+        x = x.reshape((-1,) + tuple(x.shape[-2:]))
+    L, ncols = x.shape[-2], x.shape[-1]
+    nmat = x.shape[0] if x.dim() == 3 else 1
+    mat_stride = x.stride(0) if x.dim() == 3 else L * x.stride(-2)
+    key = (L, ncols, nmat, x.stride(-2), mat_stride, bool(inverse), x.device)
+    with _cache_lock:
+        plan = _col_cache.get(key)
+        if plan is None:
+            plan = ColumnPlan(L, ncols, nmat, x.stride(-2), mat_stride,
+                              B.FFT_INVERSE if inverse else B.FFT_FORWARD, device=x.device)
+            _col_cache[key] = plan
+            while len(_col_cache) > _CACHE_MAX:
+                _col_cache.popitem(last=False)[1].close()
+        else:
+            _col_cache.move_to_end(key)
+    out = torch.empty_strided(x.shape, x.stride(), dtype=x.dtype, device=x.device)
+    plan(x, out)
+    return out.reshape(lead + (L, ncols)) if len(lead) > 1 else out
+
+
+_col_cache: "collections.OrderedDict[tuple, ColumnPlan]" = collections.OrderedDict()
 
 
 class _SpectralFilterFn(torch.autograd.Function):

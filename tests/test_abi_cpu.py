@@ -137,3 +137,17 @@ def test_filter_entry_points_validate_on_host(L):
     assert L.fft_filter_grad_h_workspace(8192, 33) == 2 * 8192 * 8
     assert L.fft_filter_grad_h(16, 16, 16, 12, 1, 16, None) == INVALID_SIZE
     assert L.fft_filter_grad_h(16, 16, 16, 256, 1, None, None) == INVALID_VALUE
+
+
+def test_column_plan_validates_on_host(L):
+    h = ctypes.c_void_p(1234)
+    assert L.fft_plan_columns(None, 256, 16, 1, 16, 4096, -1, 0) == INVALID_VALUE
+    assert L.fft_plan_columns(ctypes.byref(h), 8, 16, 1, 16, 128, -1, 0) == INVALID_SIZE
+    assert h.value is None
+    assert L.fft_plan_columns(ctypes.byref(h), 8192, 16, 1, 16, 1 << 17, -1, 0) == INVALID_SIZE
+    assert L.fft_plan_columns(ctypes.byref(h), 256, 17, 1, 17, 256 * 17, -1, 0) == INVALID_SIZE
+    assert L.fft_plan_columns(ctypes.byref(h), 4096, 6, 1, 6, 4096 * 6, -1, 0) == INVALID_SIZE
+    assert L.fft_plan_columns(ctypes.byref(h), 256, 16, 1, 8, 4096, -1, 0) == INVALID_VALUE
+    assert L.fft_plan_columns(ctypes.byref(h), 256, 16, 2, 16, 1000, -1, 0) == INVALID_VALUE
+    assert L.fft_plan_columns(ctypes.byref(h), 256, 16, 1, 16, 4096, 0, 0) == INVALID_VALUE
+    assert L.fft_plan_columns(ctypes.byref(h), 256, 16, 1, 16, 4096, -1, 0x4) == INVALID_VALUE
