@@ -319,7 +319,8 @@ fft_status_t fft_filter_backward(fft_plan_t plan, const void *g_y, const void *H
  * columns gets an L-point transform (W_L = e^{-2 pi i / L}, forward
  * unnormalised, inverse scaled by 1/L unless FFT_FLAG_UNNORMALIZED_INVERSE).
  * L: power of two in [16, 4096].  ncols: a multiple of the kernel's column
- * tile (16 for L <= 1024, 8 for 2048, 4 for 4096), else FFT_ERR_INVALID_SIZE.
+ * tile (16 for L <= 512, 8 for 1024 and 2048, 4 for 4096), else
+ * FFT_ERR_INVALID_SIZE.
  * row_stride >= ncols and < 2^31; mat_stride >= (L - 1) * row_stride + ncols
  * (matrices do not overlap); nmat >= 0 (0: exec does nothing).  Execute with
  * fft_exec(plan, in, out, stream): device pointers, 8-byte aligned, in == out

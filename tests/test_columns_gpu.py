@@ -12,7 +12,7 @@ from gpu_util import NTHREADS, TOL_FP32, rel_l2_rows, to_dev, to_host
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TILE = {16: 16, 64: 16, 256: 16, 512: 16, 1024: 16, 2048: 8, 4096: 4}
+TILE = {16: 16, 64: 16, 256: 16, 512: 16, 1024: 8, 2048: 8, 4096: 4}
 
 
 @pytest.fixture(scope="module", autouse=True)
