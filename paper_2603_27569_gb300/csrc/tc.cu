@@ -47,7 +47,7 @@ namespace fftgb {
 struct TcArgs {
   const float2 *in;
   float2 *out;
-  const float2 *tw;       // pass tables of the schedule 16, 16[, 16][, 4]
+  const float2 *tw;       // N = 16384: the radix-4 tail's table (stride 4096, radix 4)
   const float2 *twx;      // exchange twiddles in TMEM-row order: [stage][j][row]
   const uint4 *bimg;      // this direction's G image: hi plane, lo plane (2 KiB each)
   int *status;            // FFT_ERR_TIMEOUT if an MMA completion wait ran out
@@ -107,9 +107,6 @@ template <int SBO>
 __host__ __device__ constexpr int tc_rowoff(int m) {
   return (m >> 3) * SBO + (m & 7) * 16;
 }
-
-// Twiddle-table offset of pass s (s >= 1) of the schedule 16, 16, 16, 4.
-__host__ __device__ constexpr int tc_twoff(int s) { return s == 1 ? 0 : s == 2 ? 240 : 4080; }
 
 // 16-bit split of (v0, v1): hi = round(v), lo = round(v - hi), packed two per u32.
 template <int PREC>
@@ -370,7 +367,7 @@ tc_kernel(TcArgs a) {
         // whose outputs j are the four points of radix-4 butterfly 256 j + k.
         static_assert(N == 16384 && TPT == 4 && NW == 8, "tail mapping");
         const int k = 128 * g4 + 32 * q4 + lane;
-        const float2 *tw3 = a.tw + tc_twoff(3);
+        const float2 *tw3 = a.tw;  // W_16384^{v it}: entry (v - 1) * 4096 + it
 #pragma unroll 1
         for (int jc = 0; jc < 4; ++jc) {
           uint32_t r[4][8];
@@ -515,13 +512,20 @@ fft_status_t tc_plan(fft_plan_impl *pl) {
           cudaSuccess || occ < 1)
     return FFT_ERR_CUDA;
   st->grid_cap = st->persist ? (int64_t)occ * sms : 0x7fffffffLL;
-  // twiddle tables: schedule 16, 16[, 16][, 4]
-  KernelEntry k{};
-  k.npass = pl->N == 256 ? 2 : pl->N == 4096 ? 3 : 4;
-  for (int i = 0; i < 3; ++i) k.radix[i] = 16;
-  if (pl->N == 16384) k.radix[3] = 4;
-  int64_t off = 0;
-  fft_status_t s = build_twiddles(pl, pass_segments(k, off));
+  // The TC stages take their twiddles from the per-row tables (d_twx); only
+  // N = 16384's radix-4 tail (stride 4096) reads a pass table.
+  std::vector<TwSeg> segs;
+  if (pl->N == 16384) {
+    TwSeg g;
+    g.offset = 0;
+    g.count = 3 * 4096;
+    g.kind = 0;
+    g.p = 4096;
+    g.r = 4;
+    g.M = 16384;
+    segs.push_back(g);
+  }
+  fft_status_t s = build_twiddles(pl, segs);
   if (s != FFT_OK) return s;
   if (cudaMalloc(&st->d_bimg, 2 * 4096) != cudaSuccess ||
       cudaMalloc(&st->d_twx, sizeof(float2) * (size_t)st->twx_count) != cudaSuccess) {
