@@ -305,9 +305,14 @@ def run_ours(args):
     peak, peak_kind = peaks()
     per_key_ms = {k: statistics.mean(evs[s][i][0].elapsed_time(evs[s][i][1])
                                      for s in range(args.steps)) for i, k in enumerate(keys)}
+    def pct(i, q):
+        v = sorted(evs[s][i][0].elapsed_time(evs[s][i][1]) for s in range(args.steps))
+        return v[min(len(v) - 1, int(q * (len(v) - 1) + 0.5))]
+
     per_size = {}
     for N in SIZES:
         f_ms, i_ms = per_key_ms[(N, fg.FFT_FORWARD)], per_key_ms[(N, fg.FFT_INVERSE)]
+        fi, ii = keys.index((N, fg.FFT_FORWARD)), keys.index((N, fg.FFT_INVERSE))
         gbs_f = 16.0 * POINTS / (f_ms * 1e-3) / 1e9
         gbs_i = 16.0 * POINTS / (i_ms * 1e-3) / 1e9
         info = plans[(N, fg.FFT_FORWARD)].info()
@@ -316,6 +321,8 @@ def run_ours(args):
             "fwd_gflops": round(flops(N, POINTS // N) / (f_ms * 1e-3) / 1e9, 1),
             "inv_gflops": round(flops(N, POINTS // N) / (i_ms * 1e-3) / 1e9, 1),
             "fwd_frac_hbm": round(gbs_f / peak, 4), "inv_frac_hbm": round(gbs_i / peak, 4),
+            "fwd_us_p10_p50_p90": [round(pct(fi, q) * 1e3, 2) for q in (0.1, 0.5, 0.9)],
+            "inv_us_p10_p50_p90": [round(pct(ii, q) * 1e3, 2) for q in (0.1, 0.5, 0.9)],
             "path": {1: "single_cta", 2: "fourstep"}.get(info["path"], info["path"]),
             "radix": info["radix"], "points_per_thread": info["points_per_thread"],
             "twiddle_mode": info["twiddle_mode"], "grid_ctas": info["grid_ctas"],
@@ -369,6 +376,9 @@ def run_ours(args):
                                                     fg.FFT_PREC_BF16_STORAGE)
         extras["large_n"] = bench_large_n(fg, torch, dev)
         extras["azimuth_columns"] = bench_columns(fg, torch, dev)
+        extras["latency_n256_batch256"] = bench_latency(fg, torch, dev)
+        extras["fourstep_variants"] = bench_fourstep_variants(fg, torch, dev)
+        extras["cufft_context"] = bench_cufft(torch, dev, per_key_ms, fg)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nthreads = os.cpu_count() or 1
@@ -529,6 +539,77 @@ def bench_fp16_storage(fg, torch, dev, per_key_ms, precision=None):
                        "gflops": round(flops(N, POINTS // N) / (ms * 1e-3) / 1e9, 1),
                        "frac_hbm": round(8.0 * POINTS / (ms * 1e-3) / 1e9 / peaks()[0], 4),
                        "speedup_vs_fp32": round(per_key_ms[(N, fg.FFT_FORWARD)] / ms, 3)}
+    return out
+
+
+def _time_calls(torch, fn, reps=200, warm=20):
+    """CUDA-event times (ms) of reps calls of fn after warm calls."""
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    for a, b in ev:
+        a.record()
+        fn()
+        b.record()
+    torch.cuda.synchronize()
+    return sorted(a.elapsed_time(b) for a, b in ev)
+
+
+def bench_latency(fg, torch, dev):
+    """N = 256, batch 256 (512 KiB, L2-resident): per-call latency, forward."""
+    x = torch.randn(256 * 256, dtype=torch.complex64, device=dev)
+    y = torch.empty_like(x)
+    p = fg.Plan(256, 256, fg.FFT_FORWARD, device=dev)
+    t = _time_calls(torch, lambda: p(x, out=y))
+    p.close()
+    q = lambda f: t[int(f * (len(t) - 1))]
+    return {"us_p10_p50_p90": [round(q(f) * 1e3, 2) for f in (0.1, 0.5, 0.9)],
+            "gflops_p50": round(flops(256, 256) / (q(0.5) * 1e-3) / 1e9, 1),
+            "note": "L2-resident and launch-latency-bound; not an HBM-fraction case"}
+
+
+def bench_fourstep_variants(fg, torch, dev):
+    """N = 8192 and 16384 through the paper-literal four-step: two launches
+    through HBM scratch (G), and at 16384 one launch with the intermediate in
+    an L2 ring; 2^25 points per call, forward (the single-CTA in-CTA four-step
+    F is the sweep's own number)."""
+    out = {}
+    x = torch.randn(POINTS, dtype=torch.complex64, device=dev)
+    y = torch.empty_like(x)
+    cases = [(8192, "two_launch", None), (16384, "two_launch", None)]
+    for c in fg.fft_list_configs(16384):
+        if c["path"] == fg.FFT_PATH_FOURSTEP and c["l2_chunk_rows"] == 32:
+            cases.append((16384, "l2_ring_32_rows", c))
+    for N, name, cfg in cases:
+        if cfg is None:
+            p = fg.Plan(N, POINTS // N, fg.FFT_FORWARD, flags=fg.FFT_FLAG_FORCE_FOURSTEP,
+                        device=dev)
+        else:
+            p = fg.Plan(N, POINTS // N, fg.FFT_FORWARD, config=cfg, device=dev)
+        t = _time_calls(torch, lambda: p(x, out=y), reps=20, warm=3)
+        p.close()
+        ms = t[len(t) // 2]
+        out[f"{N}_{name}"] = {"us": round(ms * 1e3, 2),
+                              "frac_hbm": round(16.0 * POINTS / (ms * 1e-3) / 1e9 / peaks()[0], 4)}
+    return out
+
+
+def bench_cufft(torch, dev, per_key_ms, fg):
+    """Context only (a library comparison, never the oracle): torch.fft.fft
+    (cuFFT) on [2^25/N, N] complex64, forward, vs this library's forward."""
+    out = {}
+    try:
+        x = torch.randn(POINTS, dtype=torch.complex64, device=dev)
+        for N in SIZES:
+            v = x.view(POINTS // N, N)
+            t = _time_calls(torch, lambda: torch.fft.fft(v), reps=20, warm=3)
+            ms = t[len(t) // 2]
+            out[str(N)] = {"us": round(ms * 1e3, 2),
+                           "cufft_time_over_ours": round(ms / per_key_ms[(N, fg.FFT_FORWARD)], 3)}
+    except Exception as e:  # library context is optional
+        out["unavailable"] = str(e)[:200]
     return out
 
 
