@@ -2,9 +2,9 @@
 #include "instantiate.cuh"
 
 FFTGB_HALF(256, 16, 16, 1, 16, 16);
-FFTGB_HALF(512, 16, 8, 1, 16, 16, 2);
-FFTGB_HALF(1024, 16, 4, 1, 16, 16, 4);
-FFTGB_HALF(2048, 16, 2, 1, 16, 16, 8);
+FFTGB_HALF(512, 16, 2, 1, 16, 16, 2);
+FFTGB_HALF(1024, 16, 2, 1, 16, 16, 4);
+FFTGB_HALF(2048, 16, 1, 1, 16, 16, 8);
 FFTGB_HALF(4096, 16, 1, 0, 16, 16, 16);
 FFTGB_HALF(8192, 32, 1, 1, 32, 16, 16);
 FFTGB_HALF(16384, 32, 1, 1, 32, 32, 16);
