@@ -54,7 +54,7 @@ def peaks():
 # stays valid while these are unchanged).
 KERNEL_SOURCES = {
     "stockham": ["butterfly.cuh", "stockham.cuh", "instantiate.cuh", "registry.h",
-                 "k_small.cu", "k_mid.cu", "k_4096.cu", "k_large.cu"],
+                 "k_small.cu", "k_mid.cu", "k_4096.cu", "k_large.cu", "k_rows.cu"],
     "staged": ["butterfly.cuh", "stockham.cuh", "staged.cuh", "instantiate.cuh", "registry.h",
                "k_staged.cu"],
     "fourstep": ["butterfly.cuh", "stockham.cuh", "column.cuh", "instantiate.cuh", "registry.h",
