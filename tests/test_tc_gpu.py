@@ -50,17 +50,20 @@ def test_split_precision_error_vs_oracle(prec, N, dist, direction):
     assert err.max() <= BOUND[prec]
 
 
+@pytest.mark.parametrize("prec", ["fp16x2", "bf16x2"])
 @pytest.mark.parametrize("N", [4096, 16384])
-def test_config5_batch_sampled_rows(N):
-    # the config's batch (16384 rows); 64 sampled rows checked against the oracle
+def test_config5_batch_sampled_rows(N, prec):
+    # the config's batch (16384 rows), N(0,1); a seeded sample of 512 rows
+    # (first and last included) checked against the oracle
     batch = 16384
     x = synth.gaussian((batch, N), seed=0)
-    y = run_tc(x, fg.FFT_FORWARD, "fp16x2")
+    y = run_tc(x, fg.FFT_FORWARD, prec)
     rng = np.random.Generator(np.random.PCG64(11))
-    rows = np.unique(np.concatenate([[0, batch - 1], rng.integers(0, batch, 62)]))
+    rows = np.unique(np.concatenate([[0, batch - 1], rng.choice(batch, 510, replace=False)]))
     err = rel_l2_rows(y[rows], oracle.fft(x[rows], nthreads=NTHREADS))
-    print(f"\nTC fp16x2 N={N} batch {batch}: sampled max rel L2 {err.max():.3e}")
-    assert err.max() <= TOL_SPLIT
+    print(f"\nTC {prec} N={N} batch {batch}: {len(rows)} sampled rows, max rel L2 "
+          f"{err.max():.3e} median {np.median(err):.3e}")
+    assert err.max() <= BOUND[prec]
     assert np.isfinite(y).all()
 
 
