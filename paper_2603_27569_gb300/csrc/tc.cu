@@ -268,6 +268,12 @@ tc_kernel(TcArgs a) {
   unsigned mph = 0;  // completed phases of the MMA mbarrier
   for (long long grp = blockIdx.x; grp < ngroups; grp += C::PERSIST ? gridDim.x : ngroups) {
     const long long row0 = grp * C::TB;
+    if (C::PERSIST && warp == 0 && grp + gridDim.x < ngroups) {
+      // the next group's rows into L2 while this one runs (bulk prefetch)
+      const long long nxt = grp + gridDim.x;
+      const long long rows = min((long long)C::TB, a.batch - nxt * C::TB);
+      prefetch_l2_warp(a.in + nxt * C::TB * N, rows * N * (long long)sizeof(float2), lane);
+    }
     // Stage 0 operand: lanes take consecutive butterflies and each writes its
     // butterfly's whole row (four 16-byte chunks per plane).
 #pragma unroll
