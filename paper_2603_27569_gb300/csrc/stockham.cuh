@@ -10,7 +10,10 @@
 // the rows are in natural order (no bit reversal, Sec. II-B).
 //
 // With r < P a thread runs P / r butterflies per pass, i = t + q T, so its
-// read set is always {t + m T : m < P} and needs no per-pass reshuffle.
+// read set is always {t + m T : m < P} and needs no per-pass reshuffle.  A
+// last pass with two butterflies per thread takes butterflies 2t and 2t + 1
+// instead (pairable<>), so its exchange read, twiddle loads and output
+// stores are 16-byte accesses.
 //
 // Memory: pass 0 reads straight from global memory into registers and the
 // last pass stores straight from registers (the device-memory bypass of
@@ -69,50 +72,104 @@ __host__ __device__ constexpr bool tw_loaded(int j) {
   return j == 1 || (r == 4 && j == 2) || (r >= 8 && j == 4) || (r == 32 && j == 16);
 }
 
-// The r - 1 twiddles W^{j k}, j = 1 .. r-1, of one butterfly.
-//   TWM = 0: every one read from the pass table (row j - 1).
-//   TWM = 1: rows 1, 4 (and 2 for r = 4, 16 for r = 32) read; the others
-//            formed as products W^{j k} = W^{a k} W^{b k}, a + b = j, along a
-//            tree of depth <= 3 (<= 4 for r = 32).  This trades r - 3 table
-//            reads (L1 traffic) for as many complex multiplies.
-template <int r, int p, int TWM>
-__device__ __forceinline__ void load_twiddles(float2 (&w)[r], const float2 *__restrict__ tws, int k) {
-  if constexpr (TWM == 0) {
+// Twiddle mode 1: form the rows that are not read as products
+// W^{j k} = W^{a k} W^{b k}, a + b = j, along a tree of depth <= 3 (<= 4 for
+// r = 32), from rows 1, 4 (and 2 for r = 4, 16 for r = 32).
+template <int r>
+__device__ __forceinline__ void derive_twiddles(float2 (&w)[r]) {
 #pragma unroll
-    for (int j = 1; j < r; ++j) w[j] = __ldg(tws + (j - 1) * p + k);
-  } else {
-#pragma unroll
-    for (int j = 1; j < r; ++j)
-      if (tw_loaded<r>(j)) w[j] = __ldg(tws + (j - 1) * p + k);
-#pragma unroll
-    for (int j = 2; j < r; ++j) {
-      if (tw_loaded<r>(j)) continue;
-      if (j < 4) {
-        w[j] = cmul(w[j - 1], w[1]);               // w2 = w1 w1, w3 = w2 w1
-      } else if (j % 4 == 0) {
-        // w8 = w4 w4, w12 = w8 w4, w20 = w16 w4, w24 = w16 w8, w28 = w24 w4
-        const int a = (j >= 16 && r == 32) ? 16 : 4 * ((j / 4) / 2);
-        w[j] = cmul(w[a], w[j - a]);
-      } else {
-        const int base = j & ~3;                   // w_{4a+b} = w_{4a} w_b
-        w[j] = cmul(w[base], w[j - base]);
-      }
+  for (int j = 2; j < r; ++j) {
+    if (tw_loaded<r>(j)) continue;
+    if (j < 4) {
+      w[j] = cmul(w[j - 1], w[1]);               // w2 = w1 w1, w3 = w2 w1
+    } else if (j % 4 == 0) {
+      // w8 = w4 w4, w12 = w8 w4, w20 = w16 w4, w24 = w16 w8, w28 = w24 w4
+      const int a = (j >= 16 && r == 32) ? 16 : 4 * ((j / 4) / 2);
+      w[j] = cmul(w[a], w[j - a]);
+    } else {
+      const int base = j & ~3;                   // w_{4a+b} = w_{4a} w_b
+      w[j] = cmul(w[base], w[j - base]);
     }
   }
 }
 
+// The r - 1 twiddles W^{j k}, j = 1 .. r-1, of one butterfly.
+//   TWM = 0: every one read from the pass table (row j - 1).
+//   TWM = 1: the rows tw_loaded<r> names read, the others derived
+//            (derive_twiddles).  This trades r - 3 table reads (L1 traffic)
+//            for as many complex multiplies.
+template <int r, int p, int TWM>
+__device__ __forceinline__ void load_twiddles(float2 (&w)[r], const float2 *__restrict__ tws, int k) {
+#pragma unroll
+  for (int j = 1; j < r; ++j)
+    if (TWM == 0 || tw_loaded<r>(j)) w[j] = __ldg(tws + (j - 1) * p + k);
+  if constexpr (TWM == 1) derive_twiddles<r>(w);
+}
+
+// The twiddles of two butterflies with k0 and k0 + 1 (k0 even): their
+// entries of each table row are adjacent, so one 16-byte load gives both.
+template <int r, int p, int TWM>
+__device__ __forceinline__ void load_twiddles_pair(float2 (&w0)[r], float2 (&w1)[r],
+                                                   const float2 *__restrict__ tws, int k0) {
+#pragma unroll
+  for (int j = 1; j < r; ++j)
+    if (TWM == 0 || tw_loaded<r>(j)) {
+      const float4 v = __ldg(reinterpret_cast<const float4 *>(tws + (j - 1) * p + k0));
+      w0[j] = make_float2(v.x, v.y);
+      w1[j] = make_float2(v.z, v.w);
+    }
+  if constexpr (TWM == 1) {
+    derive_twiddles<r>(w0);
+    derive_twiddles<r>(w1);
+  }
+}
+
+// Butterfly of register group q of thread lt in a pass of radix r = P / Q.
+// Plain: butterflies lt + q T.  Paired (last pass, Q = 2): butterflies 2 lt
+// and 2 lt + 1.  In the last pass (p = N / r) butterfly i reads point
+// i + j N / r and writes output i + j N / r, so a paired thread's two points
+// (and two outputs) of each j sit side by side: one 16-byte shared load and
+// one 16-byte global store instead of two 8-byte ones.
+template <int T, int Q, bool PAIRED>
+__device__ __forceinline__ int bfly(int lt, int q) {
+  if constexpr (PAIRED) {
+    static_assert(Q == 2, "paired passes hold two butterflies per thread");
+    return 2 * lt + q;
+  } else {
+    return lt + q * T;
+  }
+}
+
+// Can schedule SC end in a paired pass?  Two butterflies per thread in the
+// last pass, and at least three passes so that the exchange read before it
+// uses a layout swz<p, r> with p >= 2, which keeps index pairs (2x, 2x + 1)
+// adjacent (the swizzle only permutes bits 1..3).
+template <int N, int P, class SC>
+__host__ __device__ constexpr bool pairable() {
+  return SC::npass >= 3 && P / SC::radix[SC::npass - 1] == 2;
+}
+
 // Twiddle + butterflies of pass S for every butterfly q of this thread.
-template <int N, int P, int D, class SC, int S, int TWM>
+template <int N, int P, int D, class SC, int S, int TWM, bool PAIRED = false>
 __device__ __forceinline__ void pass_compute(float2 (&a)[P], int lt, const float2 *__restrict__ tw) {
   constexpr int r = SC::radix[S];
   constexpr int p = SC::stride(S);
   constexpr int T = N / P;
   constexpr int Q = P / r;
-  if constexpr (S > 0) {
+  if constexpr (S > 0 && PAIRED) {
+    // k of butterflies 2 lt, 2 lt + 1 (p even): 2 lt mod p and one more
+    float2 w0[r], w1[r];
+    load_twiddles_pair<r, p, TWM>(w0, w1, tw + SC::tw_offset(S), bfly<T, Q, true>(lt, 0) & (p - 1));
+#pragma unroll
+    for (int j = 1; j < r; ++j) {
+      a[j * Q] = cmul_dir<D>(a[j * Q], w0[j]);
+      a[1 + j * Q] = cmul_dir<D>(a[1 + j * Q], w1[j]);
+    }
+  } else if constexpr (S > 0) {
     const float2 *tws = tw + SC::tw_offset(S);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      const int i = lt + q * T;
+      const int i = bfly<T, Q, PAIRED>(lt, q);
       const int k = i & (p - 1);
       float2 w[r];
       load_twiddles<r, p, TWM>(w, tws, k);
@@ -163,14 +220,29 @@ __device__ __forceinline__ void pass_write(const float2 (&a)[P], int lt, float2 
   }
 }
 
-// Read the next pass's points {lt + m T} from the buffer written by pass S.
-template <int N, int P, class SC, int S, class LY>
+// Read the next pass's points {lt + m T} from the buffer written by pass S
+// (PAIRED: the points of the next pass's paired butterflies, register
+// q + 2 j = point j of butterfly bfly(lt, q), as 16-byte pairs).
+template <int N, int P, class SC, int S, class LY, bool PAIRED = false>
 __device__ __forceinline__ void pass_read(float2 (&a)[P], int lt, const float2 *buf, const LY &ly) {
   constexpr int r = SC::radix[S];
   constexpr int p = SC::stride(S);
   constexpr int T = N / P;
+  if constexpr (PAIRED) {
+    static_assert(p >= 2, "paired reads need a layout that keeps pairs adjacent");
+    constexpr int rn = SC::radix[S + 1];
+    const int i0 = bfly<T, P / rn, true>(lt, 0);
 #pragma unroll
-  for (int m = 0; m < P; ++m) a[m] = buf[ly.template at<p, r>(lt + m * T)];
+    for (int j = 0; j < P / 2; ++j) {
+      const float4 v =
+          *reinterpret_cast<const float4 *>(buf + ly.template at<p, r>(i0 + j * (N / rn)));
+      a[2 * j] = make_float2(v.x, v.y);
+      a[2 * j + 1] = make_float2(v.z, v.w);
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < P; ++m) a[m] = buf[ly.template at<p, r>(lt + m * T)];
+  }
 }
 
 // Passes S .. npass-1.  On entry a[] holds pass S's inputs.  On return a[]
@@ -187,17 +259,21 @@ struct NamedBarrier {
   }
 };
 
-template <int N, int P, int D, class SC, int S, class LY, int TWM = 0, class BR = CtaBarrier>
+// PAIR_LAST: the last pass runs paired butterflies (its outputs leave as
+// 16-byte pairs, see final_index_pair).
+template <int N, int P, int D, class SC, int S, class LY, int TWM = 0, class BR = CtaBarrier,
+          bool PAIR_LAST = false>
 __device__ __forceinline__ void run_passes(float2 (&a)[P], int lt, float2 *buf,
                                            const float2 *__restrict__ tw, const LY &ly,
                                            const BR &br = BR{}) {
-  pass_compute<N, P, D, SC, S, TWM>(a, lt, tw);
+  constexpr bool PAIRED_HERE = PAIR_LAST && S + 1 == SC::npass;
+  pass_compute<N, P, D, SC, S, TWM, PAIRED_HERE>(a, lt, tw);
   if constexpr (S + 1 < SC::npass) {
     if constexpr (S > 0) br.sync();  // every read of the buffer is done
     pass_write<N, P, SC, S>(a, lt, buf, ly);
     br.sync();
-    pass_read<N, P, SC, S>(a, lt, buf, ly);
-    run_passes<N, P, D, SC, S + 1, LY, TWM, BR>(a, lt, buf, tw, ly, br);
+    pass_read<N, P, SC, S, LY, PAIR_LAST && S + 2 == SC::npass>(a, lt, buf, ly);
+    run_passes<N, P, D, SC, S + 1, LY, TWM, BR, PAIR_LAST>(a, lt, buf, tw, ly, br);
   }
 }
 
@@ -210,6 +286,15 @@ __device__ __forceinline__ int final_index(int lt, int m) {
   constexpr int T = N / P;
   const int q = m % Q, j = m / Q;
   return lt + q * T + j * (N / r);
+}
+
+// Paired last pass: register pair (2 j, 2 j + 1) holds outputs i0 + j N / r
+// and i0 + 1 + j N / r (i0 = bfly(lt, 0)), adjacent in the output row.
+template <int N, int P, class SC>
+__device__ __forceinline__ int final_index_pair(int lt, int j) {
+  constexpr int r = SC::radix[SC::npass - 1];
+  constexpr int T = N / P;
+  return bfly<T, P / r, true>(lt, 0) + j * (N / r);
 }
 
 // L2 prefetch of `bytes` (a multiple of 16) starting at p, issued by the 32
@@ -231,6 +316,7 @@ __device__ __forceinline__ void prefetch_l2_warp(const void *p, long long bytes,
 template <int N, int P, int TB, int D, class SC, int TWM>
 __global__ void __launch_bounds__(TB *(N / P))
 stockham_kernel(StockhamArgs args) {
+  constexpr bool PAIR_LAST = pairable<N, P, SC>();
   static_assert(SC::product() == N, "radix schedule must multiply to N");
   static_assert(P % SC::max_radix() == 0, "every radix must divide P");
   constexpr int T = N / P;
@@ -264,12 +350,22 @@ stockham_kernel(StockhamArgs args) {
     float2 *bufp = buf;
     int ltp = lt;
     asm volatile("" : "+l"(twp), "+l"(bufp), "+r"(ltp));
-    run_passes<N, P, D, SC, 0, SwizzledRow, TWM>(a, ltp, bufp, twp, SwizzledRow{});
+    run_passes<N, P, D, SC, 0, SwizzledRow, TWM, CtaBarrier, PAIR_LAST>(a, ltp, bufp, twp,
+                                                                         SwizzledRow{});
     if (active) {
       float2 *dst = args.out + row * N;
       const float s = args.scale;
+      if constexpr (PAIR_LAST) {
 #pragma unroll
-      for (int m = 0; m < P; ++m) __stcs(dst + final_index<N, P, SC>(ltp, m), cscale(a[m], s));
+        for (int j = 0; j < P / 2; ++j) {
+          const float2 u = cscale(a[2 * j], s), v = cscale(a[2 * j + 1], s);
+          __stcs(reinterpret_cast<float4 *>(dst + final_index_pair<N, P, SC>(ltp, j)),
+                 make_float4(u.x, u.y, v.x, v.y));
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < P; ++m) __stcs(dst + final_index<N, P, SC>(ltp, m), cscale(a[m], s));
+      }
     }
     if (next < ntiles) __syncthreads();  // the next tile rewrites the buffer
   }
