@@ -59,6 +59,8 @@ KERNEL_SOURCES = {
                "k_staged.cu"],
     "fourstep": ["butterfly.cuh", "stockham.cuh", "column.cuh", "instantiate.cuh", "registry.h",
                  "k_column.cu"],
+    "cluster": ["butterfly.cuh", "stockham.cuh", "cluster.cuh", "instantiate.cuh", "registry.h",
+                "k_cluster.cu", "k_cluster_big.cu"],
 }
 
 
@@ -641,14 +643,16 @@ def bench_columns(fg, torch, dev):
 
 
 def bench_large_n(fg, torch, dev):
-    """N = 2^15..2^20 (beyond one CTA: the two-phase four-step), 2^25 points
-    per call, forward, default plan (split chosen by the planner)."""
+    """N = 2^15..2^20 (beyond one CTA: 2-CTA clusters at 2^15, the two-phase
+    four-step above, and the four-step forced at 2^15 for comparison), 2^25
+    points per call, forward, default plans."""
     out = {}
     x = torch.randn(POINTS, dtype=torch.complex64, device=dev)
     y = torch.empty_like(x)
-    for e in range(15, 21):
-        N = 1 << e
-        p = fg.Plan(N, POINTS // N, fg.FFT_FORWARD, device=dev)
+    for key in [str(1 << e) for e in range(15, 21)] + ["32768_fourstep"]:
+        N = int(key.split("_")[0])
+        flags = fg.FFT_FLAG_FORCE_FOURSTEP if key.endswith("fourstep") else 0
+        p = fg.Plan(N, POINTS // N, fg.FFT_FORWARD, device=dev, flags=flags)
         for _ in range(3):
             p(x, out=y)
         torch.cuda.synchronize()
@@ -662,9 +666,10 @@ def bench_large_n(fg, torch, dev):
         ms = a.elapsed_time(b) / reps
         info = p.info()
         p.close()
-        out[str(N)] = {"us": round(ms * 1e3, 2), "n1": info["n1"], "n2": info["n2"],
-                       "gflops": round(flops(N, POINTS // N) / (ms * 1e-3) / 1e9, 1),
-                       "frac_hbm": round(16.0 * POINTS / (ms * 1e-3) / 1e9 / peaks()[0], 4)}
+        out[key] = {"us": round(ms * 1e3, 2), "n1": info["n1"], "n2": info["n2"],
+                    "cluster_split": info["cluster_split"],
+                    "gflops": round(flops(N, POINTS // N) / (ms * 1e-3) / 1e9, 1),
+                    "frac_hbm": round(16.0 * POINTS / (ms * 1e-3) / 1e9 / peaks()[0], 4)}
     return out
 
 

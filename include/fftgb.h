@@ -126,9 +126,10 @@ typedef struct {
     int tma_slabs;          /* > 0: TMA-staged persistent kernel keeping this many
                                slabs of the next row in a shared-memory ring;
                                0: pass 0 loads straight from global memory      */
-    int cluster_split;      /* 2: each row on a 2-CTA thread-block cluster (halves
-                               of N/2 points combined through distributed shared
-                               memory); 0: one CTA per row                      */
+    int cluster_split;      /* K = 2, 4, 8: each row on a cluster of K CTAs, each
+                               transforming an N/K-point part, combined through
+                               distributed shared memory (persistent clusters,
+                               one HBM pass; N up to 131072); 0: one CTA per row */
     int l2_chunk_rows;      /* four-step with n1 == n2 only.  > 0: both phases in
                                one persistent launch; rows are cut into chunks of
                                this many rows whose intermediate stays in a ring
@@ -142,10 +143,14 @@ const char *fft_status_string(fft_status_t status);
 
 /*
  * fft_plan — plan `batch` transforms of length N in one direction.
- * N: power of two, 2 <= N <= 2^20.  Up to 16384 a row fits one CTA; above
- * that only the two-phase four-step runs (N = n1 * n2 with a phase-1 length
- * n2 <= 256 and a phase-2 length n1 <= 4096; its intermediate doubles the
- * HBM traffic).  batch >= 0 (0 makes a valid plan whose
+ * N: power of two, 2 <= N <= 2^20.  Up to 16384 a row fits one CTA.  At
+ * 32768 a row runs on a 2-CTA thread-block cluster (two 16384-point halves
+ * combined through distributed shared memory, one HBM pass; the plan's info
+ * reports path FFT_PATH_SINGLE_CTA with cluster_split 2).  Above that the
+ * two-phase four-step runs (N = n1 * n2 with a phase-1 length n2 <= 256 and
+ * a phase-2 length n1 <= 4096; its intermediate doubles the HBM traffic);
+ * FFT_FLAG_FORCE_FOURSTEP selects it at 32768 too.  batch >= 0 (0 makes a
+ * valid plan whose
  * exec does nothing).  direction: FFT_FORWARD or FFT_INVERSE.
  * Allocates and fills the plan's twiddle tables on the current device
  * (generated in FP64 on the GPU, rounded to FP32) and synchronises once.
@@ -166,7 +171,9 @@ fft_status_t fft_plan_ex(fft_plan_t *out, int N, int64_t batch, int direction,
 /*
  * fft_list_configs — enumerate the FP32 execution configurations compiled
  * into this library for length N: every single-CTA Stockham variant (radix
- * schedule, points per thread, transforms per CTA) and every four-step split.
+ * schedule, points per thread, transforms per CTA), every cluster
+ * configuration (cluster_split K, N = 8192 .. 65536) and every four-step
+ * split.
  * Writes min(count, capacity) entries to out (out may be NULL) and returns
  * the total count (0 for an unsupported N).
  */

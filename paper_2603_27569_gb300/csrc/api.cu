@@ -3,10 +3,11 @@
 // Planning follows the synthesis rules of the paper (Sec. IV-D) re-derived
 // for GB300: a transform whose N points fit one CTA's shared memory (every N
 // up to 16384 = 128 KiB, within the 227 KiB a CTA may use) runs as a
-// single-CTA Stockham kernel; the two-phase four-step path (Sec. IV-B,
-// Eq. 2) splits N = N1 N2 into column FFTs plus twiddle, then row FFTs,
-// through a device intermediate.  The autotuner's cache may override either
-// choice per (N, direction, precision).
+// single-CTA Stockham kernel; N = 32768 runs on 2-CTA clusters (cluster.cuh,
+// the four-step with N1 = 2 in one HBM pass); the two-phase four-step path
+// (Sec. IV-B, Eq. 2) splits N = N1 N2 into column FFTs plus twiddle, then row
+// FFTs, through a device intermediate.  The autotuner's cache may override
+// the choice per (N, direction, precision) for N <= 16384.
 //
 // Twiddle tables (Sec. V-A/V-B compute them with a sincos chain; here they are
 // precomputed once per plan): every entry W_M^e = exp(-2 pi i e / M) is
@@ -65,9 +66,11 @@ const KernelEntry *find_staged(int N, int P, int C, const int *radix, int npass,
   return nullptr;
 }
 
-const KernelEntry *find_kind(int kind, int N, int P, const int *radix, int npass, int twm) {
+const KernelEntry *find_split(int N, int K, int P, const int *radix, int npass, int twm) {
   for (const auto &e : kernel_registry()) {
-    if (e.kind != kind || e.N != N || e.P != P || e.npass != npass || e.twm != twm) continue;
+    if (e.kind != KIND_SPLIT || e.N != N || e.split != K || e.P != P || e.npass != npass ||
+        e.twm != twm)
+      continue;
     bool same = true;
     for (int i = 0; i < npass; ++i) same = same && e.radix[i] == radix[i];
     if (same) return &e;
@@ -78,7 +81,7 @@ const KernelEntry *find_kind(int kind, int N, int P, const int *radix, int npass
 const KernelEntry *default_stockham(int N) {
   const KernelEntry *any = nullptr;
   for (const auto &e : kernel_registry()) {
-    if ((e.kind != KIND_STOCKHAM && e.kind != KIND_STAGED && e.kind != KIND_SPLIT2) || e.N != N)
+    if ((e.kind != KIND_STOCKHAM && e.kind != KIND_STAGED && e.kind != KIND_SPLIT) || e.N != N)
       continue;
     if (e.is_default) return &e;
     if (!any && e.kind == KIND_STOCKHAM) any = &e;
@@ -230,18 +233,39 @@ static fft_status_t launch_staged(const KernelEntry *k, int dir, const float2 *i
   return FFT_OK;
 }
 
-static fft_status_t launch_split2(const KernelEntry *k, int dir, const float2 *in, float2 *out,
-                                  const float2 *tw, const float2 *tw_n, int64_t rows,
-                                  float scale, cudaStream_t st) {
+// Clusters of K CTAs that can be resident at once (0 if the query fails).
+static int64_t resident_clusters(const KernelEntry *k) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = (unsigned)k->split;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)k->split);
+  cfg.blockDim = dim3((unsigned)k->threads);
+  cfg.dynamicSmemBytes = k->smem;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k->fn[0], &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+static fft_status_t launch_split(const KernelEntry *k, int dir, const float2 *in, float2 *out,
+                                 const float2 *tw, const float2 *tw_n, int64_t rows,
+                                 float scale, int64_t clusters, cudaStream_t st) {
   if (rows <= 0) return FFT_OK;
-  Split2Args a;
+  SplitArgs a;
   a.in = in;
   a.out = out;
   a.tw = tw;
   a.tw_n = tw_n;
   a.batch = rows;
   a.scale = scale;
-  const int64_t grid = 2 * rows;
+  const int64_t grid = (int64_t)k->split * (clusters > 0 && clusters < rows ? clusters : rows);
   if (grid > 0x7fffffffLL) return FFT_ERR_INVALID_SIZE;
   void *args[] = {&a};
   FFTGB_CUDA(cudaLaunchKernel(k->fn[dir > 0 ? 1 : 0], dim3((unsigned)grid), dim3(k->threads),
@@ -298,9 +322,10 @@ static fft_status_t launch_fourstep_l2(fft_plan_impl *pl, const float2 *in, floa
 fft_status_t exec_rows(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t rows,
                        cudaStream_t st) {
   if (rows <= 0) return FFT_OK;
-  if (pl->path == FFT_PATH_SINGLE_CTA && pl->k_single->kind == KIND_SPLIT2) {
-    return launch_split2(pl->k_single, pl->direction, in, out, pl->d_tw + pl->tw_single,
-                         pl->d_tw + pl->tw_big, rows, pl->scale, st);
+  if (pl->path == FFT_PATH_SINGLE_CTA && pl->k_single->kind == KIND_SPLIT) {
+    return launch_split(pl->k_single, pl->direction, in, out, pl->d_tw + pl->tw_single,
+                        pl->d_tw + pl->tw_big, rows, pl->scale, pl->grid_ctas / pl->k_single->split,
+                        st);
   }
   if (pl->path == FFT_PATH_SINGLE_CTA && pl->k_single->kind == KIND_HALFIO) {
     HalfArgs a;
@@ -505,18 +530,20 @@ static fft_status_t plan_single(fft_plan_impl *pl, const KernelEntry *k, int cta
   fft_status_t s = ensure_smem_attr(k);
   if (s != FFT_OK) return s;
   if (k->kind == KIND_STAGED) ctas_per_sm = 1;  // one resident CTA per SM by design
-  if (k->kind == KIND_SPLIT2) ctas_per_sm = 0;  // one cluster per row
-  pl->ctas_per_sm = ctas_per_sm;
-  pl->grid_ctas = ctas_per_sm != 0 ? persistent_grid(k, ctas_per_sm) : 0;
+  pl->ctas_per_sm = k->kind == KIND_SPLIT ? -1 : ctas_per_sm;
+  pl->grid_ctas = k->kind == KIND_SPLIT ? k->split * resident_clusters(k)  // persistent clusters
+                  : ctas_per_sm != 0   ? persistent_grid(k, ctas_per_sm)
+                                       : 0;
   int64_t off = 0;
   pl->tw_single = 0;
   auto segs = pass_segments(*k, off);
-  if (k->kind == KIND_SPLIT2) {  // + W_N^k for the cluster combine
+  if (k->kind == KIND_SPLIT) {  // + W_N^{r k2} at (r - 1) H + k2 for the cluster combine
     TwSeg g;
     g.offset = off;
-    g.count = pl->N;
-    g.kind = 1;
-    g.p = g.r = 0;
+    g.p = pl->N / k->split;
+    g.r = k->split;
+    g.count = (int64_t)(g.r - 1) * g.p;
+    g.kind = 0;
     g.M = pl->N;
     pl->tw_big = off;
     segs.push_back(g);
@@ -573,13 +600,21 @@ static fft_status_t plan_common(fft_plan_t *out, int N, int64_t batch, int direc
   if (cfg && (cfg->l2_chunk_rows < 0 || cfg->l2_chunk_rows > kMaxL2Rows ||
               (cfg->l2_chunk_rows > 0 && cfg->path != FFT_PATH_FOURSTEP)))
     return FFT_ERR_INVALID_VALUE;
-  // Beyond one CTA's reach (N > 16384) only the two-phase four-step runs
-  // (synthesis rule 3 of Sec. IV-D, one level: N = n1 * n2, n1, n2 <= 256).
+  // Beyond one CTA's reach (N > 16384): a built-in cluster configuration
+  // (a row on a cluster of CTAs, one HBM pass) where one exists and was
+  // measured faster, else the two-phase four-step (synthesis rule 3 of
+  // Sec. IV-D, one level: N = n1 * n2, n2 <= 256, n1 <= 4096).
+  const KernelEntry *big_default = nullptr;
   if (N > kMaxSingleN) {
     if (precision != FFT_PREC_FP32 || (flags & FFT_FLAG_FORCE_SINGLE_CTA))
       return FFT_ERR_NOT_SUPPORTED;
-    if (cfg && cfg->path != FFT_PATH_FOURSTEP) return FFT_ERR_NOT_SUPPORTED;
-    flags |= FFT_FLAG_FORCE_FOURSTEP;
+    const bool split = cfg && cfg->path == FFT_PATH_SINGLE_CTA && cfg->cluster_split > 0;
+    if (cfg && cfg->path != FFT_PATH_FOURSTEP && !split) return FFT_ERR_NOT_SUPPORTED;
+    if (!cfg && !(flags & FFT_FLAG_FORCE_FOURSTEP)) {
+      for (const auto &e : kernel_registry())
+        if (e.kind == KIND_SPLIT && e.N == N && e.is_default) big_default = &e;
+    }
+    if (!split && !big_default) flags |= FFT_FLAG_FORCE_FOURSTEP;
   }
   fft_plan_s *h = new (std::nothrow) fft_plan_s;
   if (!h) return FFT_ERR_ALLOC;
@@ -614,9 +649,9 @@ static fft_status_t plan_common(fft_plan_t *out, int N, int64_t batch, int direc
         s = plan_fourstep(pl, cfg->n1, cfg->l2_chunk_rows);
       } else if (cfg->path == FFT_PATH_SINGLE_CTA) {
         const KernelEntry *k =
-            cfg->cluster_split == 2
-                ? find_kind(KIND_SPLIT2, N, cfg->points_per_thread, cfg->radix, cfg->num_passes,
-                            cfg->twiddle_mode)
+            cfg->cluster_split > 0
+                ? find_split(N, cfg->cluster_split, cfg->points_per_thread, cfg->radix,
+                             cfg->num_passes, cfg->twiddle_mode)
             : cfg->tma_slabs > 0
                 ? find_staged(N, cfg->points_per_thread, cfg->tma_slabs, cfg->radix,
                               cfg->num_passes, cfg->twiddle_mode)
@@ -634,6 +669,8 @@ static fft_status_t plan_common(fft_plan_t *out, int N, int64_t batch, int direc
       s = k ? plan_single(pl, k, 0) : FFT_ERR_NOT_SUPPORTED;
     } else if (precision != FFT_PREC_FP32) {
       s = tc_plan(pl);
+    } else if (big_default) {
+      s = plan_single(pl, big_default, -1);
     } else if (flags & FFT_FLAG_FORCE_FOURSTEP) {
       s = plan_fourstep(pl, 0, 0);
     } else if (flags & FFT_FLAG_FORCE_SINGLE_CTA) {
@@ -647,7 +684,7 @@ static fft_status_t plan_common(fft_plan_t *out, int N, int64_t batch, int direc
         if (s == FFT_ERR_NOT_SUPPORTED) have = false;
       } else if (have) {
         const KernelEntry *k =
-            tc.split == 2  ? find_kind(KIND_SPLIT2, N, tc.P, tc.radix, tc.npass, tc.twm)
+            tc.split > 0   ? find_split(N, tc.split, tc.P, tc.radix, tc.npass, tc.twm)
             : tc.slabs > 0 ? find_staged(N, tc.P, tc.slabs, tc.radix, tc.npass, tc.twm)
                            : find_stockham(N, tc.P, tc.TB, tc.radix, tc.npass, tc.twm);
         if (k) s = plan_single(pl, k, tc.ctas_per_sm);
@@ -706,7 +743,7 @@ int fft_list_configs(int N, fft_config_t *out, int capacity) {
     }
   }
   for (const auto &e : kernel_registry()) {
-    if (e.kind != KIND_SPLIT2 || e.N != N) continue;
+    if (e.kind != KIND_SPLIT || e.N != N) continue;
     fft_config_t c;
     memset(&c, 0, sizeof(c));
     c.path = FFT_PATH_SINGLE_CTA;
@@ -716,7 +753,8 @@ int fft_list_configs(int N, fft_config_t *out, int capacity) {
     c.num_passes = e.npass;
     for (int i = 0; i < 8; ++i) c.radix[i] = e.radix[i];
     c.twiddle_mode = e.twm;
-    c.cluster_split = 2;
+    c.cluster_split = e.split;
+    c.ctas_per_sm = -1;
     emit(c);
   }
   for (const auto &e : kernel_registry()) {
@@ -983,8 +1021,7 @@ fft_status_t fft_plan_info(fft_plan_t plan, fft_plan_info_t *info) {
   info->twiddle_mode = pl->path == FFT_PATH_SINGLE_CTA ? pl->k_single->twm : 0;
   info->grid_ctas = (int)pl->grid_ctas;
   info->tma_slabs = pl->path == FFT_PATH_SINGLE_CTA ? pl->k_single->slabs : 0;
-  info->cluster_split =
-      (pl->path == FFT_PATH_SINGLE_CTA && pl->k_single->kind == KIND_SPLIT2) ? 2 : 0;
+  info->cluster_split = pl->path == FFT_PATH_SINGLE_CTA ? pl->k_single->split : 0;
   info->l2_chunk_rows = pl->l2_rows;
   if (pl->k_l2) info->grid_ctas = (int)pl->l2_grid;
   return FFT_OK;

@@ -56,20 +56,21 @@ inline KernelEntry staged_entry() {
   return e;
 }
 
-template <int N, int P, int TWM, int DEF, class SC>
-inline KernelEntry split2_entry() {
+template <int N, int K, int P, int TWM, int DEF, class SC>
+inline KernelEntry splitk_entry() {
   KernelEntry e{};
-  e.kind = KIND_SPLIT2;
+  e.kind = KIND_SPLIT;
   e.N = N;
   e.P = P;
   e.TB = 1;
-  e.threads = (N / 2) / P;
-  e.smem = sizeof(float2) * (size_t)(N / 2);
+  e.threads = (N / K) / P;
+  e.smem = sizeof(float2) * (size_t)(N / K);
   fill_radix<SC>(e);
   e.is_default = DEF;
   e.twm = TWM;
-  e.fn[0] = (const void *)&split2_kernel<N, P, -1, SC, TWM>;
-  e.fn[1] = (const void *)&split2_kernel<N, P, +1, SC, TWM>;
+  e.split = K;
+  e.fn[0] = (const void *)&splitk_kernel<N, K, P, -1, SC, TWM>;
+  e.fn[1] = (const void *)&splitk_kernel<N, K, P, +1, SC, TWM>;
   return e;
 }
 
@@ -144,13 +145,13 @@ inline KernelEntry fourstep_l2_entry() {
       ::fftgb::staged_entry<N, P, C, 0, DEF == 1, ::fftgb::Sched<__VA_ARGS__>>()); \
   static ::fftgb::Registrar FFTGB_CAT(fftgb_reg_, __COUNTER__)(              \
       ::fftgb::staged_entry<N, P, C, 1, DEF == 2, ::fftgb::Sched<__VA_ARGS__>>())
-// FFTGB_SPLIT2(N, P, is_default, radices of N/2...): cluster-split kernel,
-// both twiddle modes (is_default as for FFTGB_STOCKHAM).
-#define FFTGB_SPLIT2(N, P, DEF, ...)                                         \
+// FFTGB_SPLITK(N, K, P, is_default, radices of N/K...): a row on a cluster
+// of K CTAs, both twiddle modes (is_default as for FFTGB_STOCKHAM).
+#define FFTGB_SPLITK(N, K, P, DEF, ...)                                      \
   static ::fftgb::Registrar FFTGB_CAT(fftgb_reg_, __COUNTER__)(              \
-      ::fftgb::split2_entry<N, P, 0, DEF == 1, ::fftgb::Sched<__VA_ARGS__>>()); \
+      ::fftgb::splitk_entry<N, K, P, 0, DEF == 1, ::fftgb::Sched<__VA_ARGS__>>()); \
   static ::fftgb::Registrar FFTGB_CAT(fftgb_reg_, __COUNTER__)(              \
-      ::fftgb::split2_entry<N, P, 1, DEF == 2, ::fftgb::Sched<__VA_ARGS__>>())
+      ::fftgb::splitk_entry<N, K, P, 1, DEF == 2, ::fftgb::Sched<__VA_ARGS__>>())
 // FFTGB_HALF(N, P, TB, twiddle mode, radices...): 16-bit-storage kernels,
 // FP16 pairs (variant 0) and BF16 pairs (variant 1).
 #define FFTGB_HALF(N, P, TB, TWM, ...)                                       \

@@ -76,7 +76,7 @@ fft_status_t cuda_status(cudaError_t e);
 fft_status_t build_twiddles(fft_plan_impl *pl, const std::vector<TwSeg> &segs);
 std::vector<TwSeg> pass_segments(const KernelEntry &k, int64_t &offset);
 const KernelEntry *find_stockham(int N, int P, int TB, const int *radix, int npass, int twm);
-const KernelEntry *find_kind(int kind, int N, int P, const int *radix, int npass, int twm);
+const KernelEntry *find_split(int N, int K, int P, const int *radix, int npass, int twm);
 const KernelEntry *default_stockham(int N);
 const KernelEntry *default_column(int L, int variant);
 fft_status_t launch_stockham(const KernelEntry *k, int dir, const float2 *in, float2 *out,

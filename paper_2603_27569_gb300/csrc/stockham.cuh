@@ -259,19 +259,26 @@ struct NamedBarrier {
   }
 };
 
+struct NoHook {
+  __device__ __forceinline__ void operator()() const {}
+};
+
 // PAIR_LAST: the last pass runs paired butterflies (its outputs leave as
-// 16-byte pairs, see final_index_pair).
+// 16-byte pairs, see final_index_pair).  hk() runs once, after the barrier
+// that follows pass 0's exchange write: by then every thread has consumed
+// its pass-0 loads.
 template <int N, int P, int D, class SC, int S, class LY, int TWM = 0, class BR = CtaBarrier,
-          bool PAIR_LAST = false>
+          bool PAIR_LAST = false, class HK = NoHook>
 __device__ __forceinline__ void run_passes(float2 (&a)[P], int lt, float2 *buf,
                                            const float2 *__restrict__ tw, const LY &ly,
-                                           const BR &br = BR{}) {
+                                           const BR &br = BR{}, const HK &hk = HK{}) {
   constexpr bool PAIRED_HERE = PAIR_LAST && S + 1 == SC::npass;
   pass_compute<N, P, D, SC, S, TWM, PAIRED_HERE>(a, lt, tw);
   if constexpr (S + 1 < SC::npass) {
     if constexpr (S > 0) br.sync();  // every read of the buffer is done
     pass_write<N, P, SC, S>(a, lt, buf, ly);
     br.sync();
+    if constexpr (S == 0) hk();
     pass_read<N, P, SC, S, LY, PAIR_LAST && S + 2 == SC::npass>(a, lt, buf, ly);
     run_passes<N, P, D, SC, S + 1, LY, TWM, BR, PAIR_LAST>(a, lt, buf, tw, ly, br);
   }
@@ -310,9 +317,9 @@ __device__ __forceinline__ void prefetch_l2_warp(const void *p, long long bytes,
 }
 
 // Persistent over tiles of TB rows: CTA c handles tiles c, c + G, c + 2G, ...
-// (G = gridDim.x; a grid of one CTA per tile runs the loop once).  Before a
-// tile's loads, warp 0 asks the bulk-copy engine to prefetch the CTA's NEXT
-// tile into L2, so HBM streams the next rows while this tile computes.
+// (G = gridDim.x; a grid of one CTA per tile runs the loop once).  Warp 0
+// asks the bulk-copy engine to prefetch the CTA's NEXT tile into L2, so HBM
+// streams the next rows while this tile computes.
 template <int N, int P, int TB, int D, class SC, int TWM>
 __global__ void __launch_bounds__(TB *(N / P))
 stockham_kernel(StockhamArgs args) {
@@ -327,11 +334,19 @@ stockham_kernel(StockhamArgs args) {
   const long long ntiles = (args.batch + TB - 1) / TB;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long next = tile + gridDim.x;
-    if (next < ntiles && threadIdx.x < 32) {
-      const long long rows = args.batch - next * TB < TB ? args.batch - next * TB : TB;
-      prefetch_l2_warp(args.in + next * TB * N, rows * N * (long long)sizeof(float2),
-                       threadIdx.x);
-    }
+    auto prefetch_next = [&]() {
+      if (next < ntiles && threadIdx.x < 32) {
+        const long long rows = args.batch - next * TB < TB ? args.batch - next * TB : TB;
+        prefetch_l2_warp(args.in + next * TB * N, rows * N * (long long)sizeof(float2),
+                         threadIdx.x);
+      }
+    };
+    // The first tile's own loads come from HBM: its prefetch of the next
+    // tile waits until they have landed (after the first exchange).  Later
+    // tiles were prefetched into L2 and prefetch theirs at once, which
+    // gives the next tile the whole tile time to arrive.
+    const bool first = tile == (long long)blockIdx.x;
+    if (SC::npass == 1 || !first) prefetch_next();
     const long long row = tile * TB + b;
     const bool active = row < args.batch;
     float2 a[P];
@@ -350,8 +365,10 @@ stockham_kernel(StockhamArgs args) {
     float2 *bufp = buf;
     int ltp = lt;
     asm volatile("" : "+l"(twp), "+l"(bufp), "+r"(ltp));
-    run_passes<N, P, D, SC, 0, SwizzledRow, TWM, CtaBarrier, PAIR_LAST>(a, ltp, bufp, twp,
-                                                                         SwizzledRow{});
+    run_passes<N, P, D, SC, 0, SwizzledRow, TWM, CtaBarrier, PAIR_LAST>(
+        a, ltp, bufp, twp, SwizzledRow{}, CtaBarrier{}, [&]() {
+          if (first) prefetch_next();
+        });
     if (active) {
       float2 *dst = args.out + row * N;
       const float s = args.scale;

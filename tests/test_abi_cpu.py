@@ -104,10 +104,11 @@ def test_configs_listed_for_every_supported_size(L):
             prod = 1
             for r in c["radix"]:
                 prod *= r
-            if c["path"] == fg.FFT_PATH_SINGLE_CTA and c["cluster_split"] == 2:
-                # each CTA of the pair transforms N/2 points
-                assert prod == N // 2
-                assert c["threads_per_cta"] == (N // 2) // c["points_per_thread"]
+            if c["path"] == fg.FFT_PATH_SINGLE_CTA and c["cluster_split"]:
+                # each CTA of the cluster transforms N/K points
+                K = c["cluster_split"]
+                assert K in (2, 4, 8) and prod == N // K
+                assert c["threads_per_cta"] == (N // K) // c["points_per_thread"]
             elif c["path"] == fg.FFT_PATH_SINGLE_CTA:
                 assert prod == N
                 assert all(c["points_per_thread"] % r == 0 for r in c["radix"])
@@ -117,11 +118,20 @@ def test_configs_listed_for_every_supported_size(L):
                 assert prod == N // c["n1"] and N % c["n1"] == 0
     assert fg.fft_list_configs(12) == []
     assert fg.fft_list_configs(1 << 21) == []
-    for e in range(15, 21):   # beyond one CTA: two-phase four-step only
+    for e in range(15, 21):   # beyond one CTA: four-step, and clusters up to 2^16
         N = 1 << e
         cfgs = fg.fft_list_configs(N)
-        assert cfgs and all(c["path"] == fg.FFT_PATH_FOURSTEP for c in cfgs)
-        for c in cfgs:
+        four = [c for c in cfgs if c["path"] == fg.FFT_PATH_FOURSTEP]
+        split = [c for c in cfgs if c["path"] == fg.FFT_PATH_SINGLE_CTA]
+        assert four and len(four) + len(split) == len(cfgs)
+        assert all(c["cluster_split"] in (2, 4, 8) for c in split)
+        assert bool(split) == (N <= 1 << 16)
+        for c in split:
+            prod = 1
+            for r in c["radix"]:
+                prod *= r
+            assert prod * c["cluster_split"] == N and prod <= 16384
+        for c in four:
             n2 = N // c["n1"]
             assert c["n1"] * n2 == N and 16 <= n2 <= 256 and c["n1"] <= 4096
     for N in (8192, 16384):

@@ -71,7 +71,7 @@ def test_every_compiled_config_matches_oracle(N, direction):
         check(x, y, direction)
 
 
-@pytest.mark.parametrize("N", [512, 1024, 2048, 4096, 8192, 16384])
+@pytest.mark.parametrize("N", [512, 1024, 2048, 4096, 8192, 16384, 32768])
 def test_full_size_sampled_rows(N):
     # the benchmark's size: 2^25 points (256 MiB) per call, batch = 2^25 / N
     batch = (1 << 25) // N
@@ -272,16 +272,23 @@ def test_host_buffer_exec_matches_device_exec(N, flags):
 
 @pytest.mark.parametrize("N", [1 << e for e in range(15, 21)])
 @pytest.mark.parametrize("direction", [fg.FFT_FORWARD, fg.FFT_INVERSE])
-def test_beyond_one_cta_fourstep(N, direction):
-    # N > 16384: the two-phase four-step (phase 1 <= 256 points, phase 2 <=
-    # 4096) is the only path; every listed split, ragged CTA tail included
+def test_beyond_one_cta(N, direction):
+    # N > 16384: 2-CTA clusters at 32768, else the two-phase four-step
+    # (phase 1 <= 256 points, phase 2 <= 4096); the four-step forced at every
+    # N; every listed configuration, ragged CTA tail included
     cfgs = fg.fft_list_configs(N)
     assert cfgs
     x = synth.gaussian((3, N), seed=N)
     y, info = run(x, direction)
+    if N == 32768:
+        assert info["path"] == fg.FFT_PATH_SINGLE_CTA and info["cluster_split"] == 2
+    else:
+        assert info["path"] == fg.FFT_PATH_FOURSTEP and info["n1"] * info["n2"] == N
+    check(x, y, direction)
+    y, info = run(x, direction, flags=fg.FFT_FLAG_FORCE_FOURSTEP)
     assert info["path"] == fg.FFT_PATH_FOURSTEP and info["n1"] * info["n2"] == N
     check(x, y, direction)
     for cfg in cfgs:
         y, info = run(x[:2], direction, config=cfg)
-        assert info["n1"] == cfg["n1"]
+        assert info["n1"] == cfg["n1"] and info["cluster_split"] == cfg["cluster_split"]
         check(x[:2], y, direction)

@@ -72,7 +72,9 @@ def test_single_buffer_rule_on_gb300():
     b = gb300_cta_bytes // g["element_bytes"]
     b_pow2 = 1 << (b.bit_length() - 1)
     assert b_pow2 == 16384
-    single = lambda N: any(c["path"] == fg.FFT_PATH_SINGLE_CTA for c in fg.fft_list_configs(N))
+    # one CTA holding the whole row (cluster configurations spread it over K CTAs)
+    single = lambda N: any(c["path"] == fg.FFT_PATH_SINGLE_CTA and not c["cluster_split"]
+                           for c in fg.fft_list_configs(N))
     assert single(b_pow2) and not single(2 * b_pow2)
 
 
