@@ -13,7 +13,7 @@
  * It is computed as a Stockham autosort factorisation (Sec. II-B) with
  * register-resident radix-8/16 DIT butterflies and radix-4/2 tails
  * (Sec. V-A, V-B), shared-memory exchange between passes, precomputed
- * twiddle tables, and a four-step decomposition (Sec. IV-B, Eq. 2) for large N.
+ * twiddle tables, and a four-step decomposition (Sec. IV-B, Eq. 3) for large N.
  *
  * Data layout (all entry points unless stated otherwise): interleaved complex
  * float32 (`float2`: re, im), transform-major: element n of transform b is at

@@ -5,7 +5,7 @@
 // up to 16384 = 128 KiB, within the 227 KiB a CTA may use) runs as a
 // single-CTA Stockham kernel; N = 32768 runs on 2-CTA clusters (cluster.cuh,
 // the four-step with N1 = 2 in one HBM pass); the two-phase four-step path
-// (Sec. IV-B, Eq. 2) splits N = N1 N2 into column FFTs plus twiddle, then row
+// (Sec. IV-B, Eq. 3) splits N = N1 N2 into column FFTs plus twiddle, then row
 // FFTs, through a device intermediate.  The autotuner's cache may override
 // the choice per (N, direction, precision) for N <= 16384.
 //

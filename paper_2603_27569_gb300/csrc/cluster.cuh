@@ -2,7 +2,7 @@
 // cluster of K CTAs (K = 2, 4, 8), exchanging through distributed shared
 // memory.  One HBM pass per row for N up to K x 16384.
 //
-// The four-step split with N1 = K (paper Sec. IV-B, Eq. 2; Sec. V-D):
+// The four-step split with N1 = K (paper Sec. IV-B, Eq. 3; Sec. V-D):
 //   n = r + K n2, k = k2 + H k1, H = N / K, r, k1 < K, n2, k2 < H
 //   CTA r:   A_r[k2] = FFT_H over n2 of x[r + K n2]        (registers + smem)
 //            B_r[k2] = A_r[k2] W_N^{r k2}                   (the four-step twiddle)

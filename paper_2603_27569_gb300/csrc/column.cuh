@@ -1,6 +1,6 @@
 // Column FFTs: batched length-L transforms down the columns of a row-major
 // matrix, C adjacent columns per CTA.  This is the building block of the
-// two-phase four-step path (paper Sec. IV-B, Eq. 2 and Sec. V-D):
+// two-phase four-step path (paper Sec. IV-B, Eq. 3 and Sec. V-D):
 //
 //   N = N1 N2, input index n = n1 + N1 n2, output index k = k2 + N2 k1.
 //   phase 1: for every n1, the N2-point FFT over n2 of x[n1 + N1 n2], times

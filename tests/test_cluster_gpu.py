@@ -1,6 +1,6 @@
 """Cluster-split kernel (a row on a cluster of K CTAs) against the FP64 oracle.
 
-The kernel computes the four-step with N1 = K (paper Sec. IV-B, Eq. 2): each
+The kernel computes the four-step with N1 = K (paper Sec. IV-B, Eq. 3): each
 CTA transforms the stride-K subsequence of a row, multiplies by W_N^{r k2},
 and the cluster combines with K-point DFTs through distributed shared memory.
 Clusters are persistent over rows, so batches larger than the resident

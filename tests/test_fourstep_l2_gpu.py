@@ -1,6 +1,6 @@
 """Single-launch four-step with the intermediate in an L2 ring (N = L * L).
 
-Both phases of the two-phase four-step (Sec. IV-B, Eq. 2) run in one
+Both phases of the two-phase four-step (Sec. IV-B, Eq. 3) run in one
 persistent launch whose work items are ordered by a device counter; a chunk's
 intermediate lives in a ring slot that is reused once its phase 2 is done.
 Batches here span many chunks, so every slot is reused several times and the
