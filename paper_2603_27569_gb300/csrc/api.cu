@@ -137,6 +137,18 @@ __global__ void gen_full_twiddles(float2 *out, int64_t M, int64_t count) {
   out[e] = make_float2(__double2float_rn(c), __double2float_rn(s));
 }
 
+// Grid: entry i * cols + c = W_M^{(i step c) mod M}, i * cols + c < count.
+__global__ void gen_grid_twiddles(float2 *out, int64_t cols, int64_t step, int64_t M,
+                                  int64_t count) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= count) return;
+  const int64_t i = idx / cols, c = idx % cols;
+  const int64_t e = ((i * step) % M) * c % M;
+  double s, co;
+  sincospi(-2.0 * (double)e / (double)M, &s, &co);
+  out[idx] = make_float2(__double2float_rn(co), __double2float_rn(s));
+}
+
 std::vector<TwSeg> pass_segments(const KernelEntry &k, int64_t &offset) {
   std::vector<TwSeg> segs;
   int p = k.radix[0];
@@ -171,6 +183,8 @@ fft_status_t build_twiddles(fft_plan_impl *pl, const std::vector<TwSeg> &segs) {
     const unsigned blocks = (unsigned)((g.count + threads - 1) / threads);
     if (g.kind == 0)
       gen_pass_twiddles<<<blocks, threads>>>(pl->d_tw + g.offset, g.p, g.r);
+    else if (g.kind == 2)
+      gen_grid_twiddles<<<blocks, threads>>>(pl->d_tw + g.offset, g.p, g.step, g.M, g.count);
     else
       gen_full_twiddles<<<blocks, threads>>>(pl->d_tw + g.offset, g.M, g.count);
     FFTGB_CUDA(cudaGetLastError());
@@ -301,7 +315,8 @@ static fft_status_t launch_fourstep_l2(fft_plan_impl *pl, const float2 *in, floa
     a.out = out + r0 * pl->N;
     a.ring = pl->d_scratch;
     a.tw = pl->d_tw + pl->tw_col1;
-    a.tw_big = pl->d_tw + pl->tw_big;
+    a.tw_a = pl->d_tw + pl->tw_big;
+    a.tw_b = pl->d_tw + pl->tw_big2;
     a.counters = pl->d_l2cnt;
     a.status = pl->d_status;
     a.batch = nr;
@@ -355,7 +370,8 @@ fft_status_t exec_rows(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t
     c1.in = in;
     c1.out = pl->d_scratch;
     c1.tw = pl->d_tw + pl->tw_col1;
-    c1.tw_big = pl->d_tw + pl->tw_big;
+    c1.tw_a = pl->d_tw + pl->tw_big;
+    c1.tw_b = pl->d_tw + pl->tw_big2;
     c1.nmat = rows;
     c1.in_mat_stride = pl->N;
     c1.out_mat_stride = pl->N;
@@ -370,7 +386,7 @@ fft_status_t exec_rows(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t
     c2.in = pl->d_scratch;
     c2.out = out;
     c2.tw = pl->d_tw + pl->tw_col2;
-    c2.tw_big = nullptr;
+    c2.tw_a = c2.tw_b = nullptr;
     c2.nmat = rows;
     c2.in_mat_stride = pl->N;
     c2.out_mat_stride = pl->N;
@@ -489,14 +505,26 @@ static fft_status_t plan_fourstep(fft_plan_impl *pl, int want_n1, int l2_rows) {
     segs.insert(segs.end(), b.begin(), b.end());
   }
   pl->tw_big = off;
-  TwSeg big;
-  big.offset = off;
-  big.count = pl->N;
-  big.kind = 1;
-  big.p = big.r = 0;
-  big.M = pl->N;
-  off += pl->N;
-  segs.push_back(big);
+  {  // phase-1 twiddle: W_N^{c lt} [lt][c] and W_N^{c T m} [m][c] (column.cuh)
+    const int P1 = pl->k_l2 ? pl->k_l2->P : pl->k_col1->P, T1 = n2 / P1;
+    TwSeg ga;
+    ga.offset = off;
+    ga.kind = 2;
+    ga.p = n1;
+    ga.r = 0;
+    ga.step = 1;
+    ga.M = pl->N;
+    ga.count = (int64_t)T1 * n1;
+    off += ga.count;
+    segs.push_back(ga);
+    TwSeg gb = ga;
+    gb.offset = off;
+    gb.step = T1;
+    gb.count = (int64_t)P1 * n1;
+    pl->tw_big2 = off;
+    off += gb.count;
+    segs.push_back(gb);
+  }
   s = build_twiddles(pl, segs);
   if (s != FFT_OK) return s;
   if (pl->k_l2) {
@@ -842,7 +870,7 @@ fft_status_t fft_exec(fft_plan_t plan, const void *in, void *out, void *stream) 
     c.in = (const float2 *)in;
     c.out = (float2 *)out;
     c.tw = pl->d_tw + pl->tw_col2;
-    c.tw_big = nullptr;
+    c.tw_a = c.tw_b = nullptr;
     c.nmat = pl->col_nmat;
     c.in_mat_stride = pl->col_mat_stride;
     c.out_mat_stride = pl->col_mat_stride;
@@ -1060,6 +1088,10 @@ fft_status_t fft_twiddle_index(fft_plan_t plan, int64_t pos, int64_t *M, int64_t
       const int64_t j = local / g.p + 1, k = local % g.p;
       *M = g.M;
       *e = j * k;
+    } else if (g.kind == 2) {
+      const int64_t i = local / g.p, c = local % g.p;
+      *M = g.M;
+      *e = ((i * g.step) % g.M) * c % g.M;
     } else {
       *M = g.M;
       *e = local;

@@ -15,6 +15,12 @@
 // columns, so every exchange is free of bank conflicts without a swizzle.
 // Phase 1 stores its result transposed (column-major) through a padded
 // shared tile so that the global store is coalesced as well.
+//
+// Phase-1 twiddle W_N^{c k} for column c and output k: register m of thread
+// lt holds k = lt + T m (T = L / P), so W_N^{c k} = W_N^{c lt} W_N^{c T m},
+// the product of two exact table entries from grids laid out [lt][c] and
+// [m][c]: a warp's loads read C consecutive columns (whole sectors) instead
+// of gathering one sector per element from a table of all N powers.
 #pragma once
 #include "stockham.cuh"
 
@@ -24,7 +30,8 @@ struct ColumnArgs {
   const float2 *in;
   float2 *out;
   const float2 *tw;      // per-pass tables of the length-L transform
-  const float2 *tw_big;  // W_{Ntot}^e, e < Ntot (phase 1 twiddle) or null
+  const float2 *tw_a;    // phase 1: W_Ntot^{c lt} at lt * ncols + c, or null
+  const float2 *tw_b;    // phase 1: W_Ntot^{c T m} at m * ncols + c
   long long nmat;        // number of matrices (batch)
   long long in_mat_stride, out_mat_stride;  // elements between matrices
   int in_row_stride;     // elements between consecutive rows of the input
@@ -57,11 +64,11 @@ column_kernel(ColumnArgs args) {
   // a[m] now holds output index final_index(lt, m) of column c0 + c.
   if constexpr (TWIDDLE) {
     const int col = c0 + c;
+    const float2 wa = __ldg(args.tw_a + (long long)lt * args.ncols + col);
 #pragma unroll
-    for (int m = 0; m < P; ++m) {
-      const int k = final_index<L, P, SC>(lt, m);
-      const int e = (col * k) & (args.ntot - 1);
-      a[m] = cmul_dir<D>(a[m], __ldg(args.tw_big + e));
+    for (int m = 0; m < P; ++m) {  // final_index(lt, m) = lt + T m
+      const float2 w = cmul(wa, __ldg(args.tw_b + (long long)m * args.ncols + col));
+      a[m] = cmul_dir<D>(a[m], w);
     }
   }
   if constexpr (TRANSPOSED) {

@@ -34,7 +34,8 @@ struct FourstepL2Args {
   float2 *out;
   float2 *ring;            // S slots of chunk_rows * N points
   const float2 *tw;        // pass tables of the L-point schedule
-  const float2 *tw_big;    // W_N^e, e < N
+  const float2 *tw_a;      // W_N^{c lt} at lt * L + c (phase-1 twiddle, as column.cuh)
+  const float2 *tw_b;      // W_N^{c T m} at m * L + c
   unsigned *counters;      // [0] items claimed, [1] CTAs finished, then nchunks phase-1
                            // done counts and nchunks phase-2 done counts; all zero
                            // between launches (the last CTA to finish clears them)
@@ -151,12 +152,11 @@ fourstep_l2_kernel(FourstepL2Args a) {
         asm volatile("" : "+l"(twp), "+l"(bufp), "+r"(ltp), "+r"(cp));
         run_passes<L, P, D, SC, 0>(v, ltp, bufp, twp, Interleaved<C>{cp});
         if (it.p1) {
-          const int col = c0 + c;  // n1
+          const int col = c0 + c;  // n1; register m holds k2 = lt + T m
+          const float2 wa = __ldg(a.tw_a + lt * L + col);
 #pragma unroll
-          for (int m = 0; m < P; ++m) {
-            const int k = final_index<L, P, SC>(lt, m);
-            v[m] = cmul_dir<D>(v[m], __ldg(a.tw_big + ((col * k) & (N - 1))));
-          }
+          for (int m = 0; m < P; ++m)
+            v[m] = cmul_dir<D>(v[m], cmul(wa, __ldg(a.tw_b + m * L + col)));
           // A[n1][k2] at slot + n1 * L + k2, through a tile padded to C + 1 columns
           constexpr int LD = C + 1;
           __syncthreads();

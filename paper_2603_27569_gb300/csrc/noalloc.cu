@@ -30,7 +30,8 @@ namespace fftgb {
 
 // Twiddle generators of the regular planner (api.cu), reused unchanged.
 __global__ void gen_pass_twiddles(float2 *out, int p, int r);
-__global__ void gen_full_twiddles(float2 *out, int64_t M, int64_t count);
+__global__ void gen_grid_twiddles(float2 *out, int64_t cols, int64_t step, int64_t M,
+                                  int64_t count);
 
 namespace {
 
@@ -46,7 +47,7 @@ static __device__ __align__(256) float2 g_tw[kTwEntries];
 struct SizeSetup {
   int n1 = 0, n2 = 0;
   const KernelEntry *k1 = nullptr, *k2 = nullptr;  // phase-1 / phase-2 column kernels
-  int64_t tw1 = 0, tw2 = 0, twbig = 0;             // offsets into g_tw
+  int64_t tw1 = 0, tw2 = 0, twa = 0, twb = 0;      // offsets into g_tw
 };
 
 struct DeviceSetup {
@@ -109,10 +110,16 @@ fft_status_t setup_device(int dev, DeviceSetup **out) {
       off = fill_pass_tables(z.k1, d.tw, off);
       z.tw2 = off;
       off = fill_pass_tables(z.k2, d.tw, off);
-      z.twbig = off;
-      gen_full_twiddles<<<(unsigned)((N + 255) / 256), 256>>>(d.tw + off, N, N);
-      off += N;
-      if (off > kTwEntries) return FFT_ERR_NOT_SUPPORTED;
+      // phase-1 twiddle grids W_N^{c lt} [lt][c] and W_N^{c T m} [m][c]
+      const int T1 = z.n2 / z.k1->P;
+      const int64_t na = (int64_t)T1 * z.n1, nb = (int64_t)z.k1->P * z.n1;
+      if (off + na + nb > kTwEntries) return FFT_ERR_NOT_SUPPORTED;
+      z.twa = off;
+      gen_grid_twiddles<<<(unsigned)((na + 255) / 256), 256>>>(d.tw + off, z.n1, 1, N, na);
+      off += na;
+      z.twb = off;
+      gen_grid_twiddles<<<(unsigned)((nb + 255) / 256), 256>>>(d.tw + off, z.n1, T1, N, nb);
+      off += nb;
     }
     if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
       return FFT_ERR_CUDA;
@@ -164,7 +171,8 @@ extern "C" fft_status_t fft_fourstep_noalloc(const void *in, void *out, int N, i
   c1.in = (const float2 *)in;
   c1.out = d->scratch;
   c1.tw = d->tw + z.tw1;
-  c1.tw_big = d->tw + z.twbig;
+  c1.tw_a = d->tw + z.twa;
+  c1.tw_b = d->tw + z.twb;
   c1.nmat = batch;
   c1.in_mat_stride = N;
   c1.out_mat_stride = N;

@@ -15,9 +15,11 @@ namespace fftgb {
 struct TwSeg {
   int64_t offset;  // first entry
   int64_t count;   // entries
-  int kind;        // 0: per-pass table W_{p r}^{j k} laid out [j-1][k]; 1: W_M^e, e < M
-  int p, r;        // kind 0
-  int64_t M;       // kind 1 (and p*r for kind 0)
+  int kind;        // 0: per-pass table W_{p r}^{j k} laid out [j-1][k]; 1: W_M^e, e < M;
+                   // 2: grid W_M^{(i step c) mod M} at i * p + c, c < p (p columns)
+  int p, r;        // kind 0 (kind 2: p = columns)
+  int64_t M;       // kinds 1 and 2 (and p*r for kind 0)
+  int64_t step = 0;  // kind 2
 };
 
 struct RaggedState;  // ragged.cu
@@ -54,6 +56,7 @@ struct fft_plan_impl {
   int64_t tw_count = 0;
   std::vector<TwSeg> tw_segs;
   int64_t tw_single = 0, tw_col1 = 0, tw_col2 = 0, tw_big = 0;  // offsets
+  int64_t tw_big2 = 0;  // four-step phase 1: W_N^{c T m} grid (tw_big: W_N^{c lt})
   // scratch (four-step intermediate)
   float2 *d_scratch = nullptr;
   int64_t scratch_bytes = 0;
