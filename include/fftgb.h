@@ -298,14 +298,18 @@ fft_status_t fft_filter_grad_h(const void *X, const void *G, void *grad_H, int N
  *
  * fft_filter_plan: plan for `batch` rows of N points, N power of two in
  *   [256, 16384] (FFT_ERR_NOT_SUPPORTED otherwise).  Owns the twiddle tables
- *   and the backward pass's per-CTA partial sums.  Free with fft_destroy.
+ *   and the backward pass's grad_H workspace (one row of sums per 32 rows).
+ *   Free with fft_destroy.
  * fft_filter_forward: y = IFFT(FFT(x) * H) (conj_h = 1: * conj(H)), inverse
  *   scaled by 1/N; if X_save is non-NULL it also receives FFT(x) (needed by
  *   the backward).  x, y, X_save: batch*N float2; H: N float2.
  * fft_filter_backward: with g_y = dL/dy (PyTorch convention),
  *   grad_x = IFFT(FFT(g_y) * conj(H)) = F^H(conj(H) * g_z), g_z = FFT(g_y)/N,
- *   grad_H = sum_rows conj(X_saved) * g_z  (per-CTA partials + fixed-order
- *   tree: bitwise reproducible on a given GPU).
+ *   grad_H = sum_rows conj(X_saved) * g_z  (sums over 32-row chunks in row
+ *   order, then a fixed-order pairwise tree: bitwise reproducible on a given
+ *   GPU).  Three kernels: g_z into grad_x's buffer, the grad_H reduction,
+ *   then grad_x in place; so grad_x may not overlap g_y or X_saved
+ *   (FFT_ERR_INVALID_VALUE).
  * Device pointers, 16-byte aligned; asynchronous on stream.
  */
 fft_status_t fft_filter_plan(fft_plan_t *out, int N, int64_t batch);

@@ -44,13 +44,22 @@ __global__ void grad_h_partial_kernel(const float2 *__restrict__ X, const float2
   const int64_t c = blockIdx.y;
   if (k >= N) return;
   const int64_t b0 = c * kRowsPerChunk;
-  const int64_t b1 = b0 + kRowsPerChunk < batch ? b0 + kRowsPerChunk : batch;
+  const int rows = (int)(batch - b0 < kRowsPerChunk ? batch - b0 : kRowsPerChunk);
+  // Unrolled over the chunk with predicated loads, so all of a thread's
+  // loads are in flight at once; the sum still runs in row order.
+  float2 xs[kRowsPerChunk], gs[kRowsPerChunk];
+#pragma unroll
+  for (int i = 0; i < kRowsPerChunk; ++i) {
+    const bool on = i < rows;
+    xs[i] = on ? __ldcs(X + (b0 + i) * N + k) : make_float2(0.f, 0.f);
+    gs[i] = on ? __ldcs(G + (b0 + i) * N + k) : make_float2(0.f, 0.f);
+  }
   float2 acc = make_float2(0.f, 0.f);
-  for (int64_t b = b0; b < b1; ++b) {
-    const float2 x = __ldg(X + b * N + k), g = __ldg(G + b * N + k);
-    // conj(x) * g
-    acc.x = fmaf(x.x, g.x, fmaf(x.y, g.y, acc.x));
-    acc.y = fmaf(x.x, g.y, fmaf(-x.y, g.x, acc.y));
+#pragma unroll
+  for (int i = 0; i < kRowsPerChunk; ++i) {
+    // conj(x) * g (zero for rows past the batch)
+    acc.x = fmaf(xs[i].x, gs[i].x, fmaf(xs[i].y, gs[i].y, acc.x));
+    acc.y = fmaf(xs[i].x, gs[i].y, fmaf(-xs[i].y, gs[i].x, acc.y));
   }
   partial[c * N + k] = acc;
 }
@@ -62,6 +71,36 @@ __global__ void grad_h_tree_kernel(float2 *partial, int N, int64_t nchunk, int64
   if (k >= N || c + h >= nchunk) return;
   float2 a = partial[c * N + k], b = partial[(c + h) * N + k];
   partial[c * N + k] = make_float2(a.x + b.x, a.y + b.y);
+}
+
+// The same pairwise tree in one launch: a CTA stages the partial sums of
+// kTreeCols frequencies for every chunk in shared memory, runs the levels
+// (same additions in the same order as grad_h_tree_kernel, so the result is
+// identical) and writes grad_H for its frequencies.  Used while the chunk
+// rows fit the shared memory (kTreeMaxChunks).
+constexpr int kTreeCols = 32;
+constexpr int kTreeThreads = 256;
+constexpr int64_t kTreeMaxChunks = 768;  // 768 x 32 x 8 B = 192 KiB
+
+__global__ void __launch_bounds__(kTreeThreads) grad_h_tree_smem_kernel(const float2 *partial,
+                                                                       float2 *out, int N,
+                                                                       int nchunk) {
+  extern __shared__ float2 tree[];  // [nchunk][kTreeCols]
+  const int k0 = blockIdx.x * kTreeCols;
+  const int f = threadIdx.x % kTreeCols, lane = threadIdx.x / kTreeCols;
+  constexpr int kLanes = kTreeThreads / kTreeCols;
+  const bool on = k0 + f < N;
+  for (int c = lane; c < nchunk; c += kLanes)
+    tree[c * kTreeCols + f] = on ? partial[(int64_t)c * N + k0 + f] : make_float2(0.f, 0.f);
+  __syncthreads();
+  for (int h = 1; h < nchunk; h *= 2) {
+    for (int c = 2 * h * lane; c + h < nchunk; c += 2 * h * kLanes) {
+      const float2 a = tree[c * kTreeCols + f], b = tree[(c + h) * kTreeCols + f];
+      tree[c * kTreeCols + f] = make_float2(a.x + b.x, a.y + b.y);
+    }
+    __syncthreads();
+  }
+  if (lane == 0 && on) out[k0 + f] = tree[f];
 }
 
 __global__ void copy_row_kernel(const float2 *src, float2 *dst, int N) {
@@ -120,6 +159,16 @@ fft_status_t fft_filter_grad_h(const void *X, const void *G, void *grad_H, int N
   float2 *part = (float2 *)work;
   grad_h_partial_kernel<<<dim3(bx, (unsigned)nchunk), threads, 0, st>>>(
       (const float2 *)X, (const float2 *)G, part, N, batch);
+  if (nchunk <= kTreeMaxChunks) {
+    const size_t smem = sizeof(float2) * (size_t)nchunk * kTreeCols;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(grad_h_tree_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return FFT_ERR_CUDA;
+    grad_h_tree_smem_kernel<<<(unsigned)((N + kTreeCols - 1) / kTreeCols), kTreeThreads, smem, st>>>(
+        part, (float2 *)grad_H, N, (int)nchunk);
+    return cuda_status(cudaGetLastError());
+  }
   for (int64_t h = 1; h < nchunk; h *= 2) {
     const int64_t groups = (nchunk + 2 * h - 1) / (2 * h);
     grad_h_tree_kernel<<<dim3(bx, (unsigned)groups), threads, 0, st>>>(part, N, nchunk, h);

@@ -101,3 +101,27 @@ def test_fft_autograd_uses_the_adjoint(N, inverse):
     gy = 2.0 * m * Tx
     want = N * oracle.ifft(gy) if not inverse else oracle.fft(gy) / N
     assert rel(g, want) <= TOL_GRAD
+
+
+@pytest.mark.parametrize("batch", [1, 33, 32 * 700, 32 * 800 + 5])
+def test_grad_h_reduction_both_tree_forms(batch):
+    # grad_H = sum_rows conj(X) * G: 32-row chunk sums, then a pairwise tree
+    # over the chunks (one launch in shared memory up to 768 chunks, level by
+    # level above); checked against the FP64 sum and bitwise run to run
+    N = 64
+    X = synth.gaussian((batch, N), seed=batch)
+    G = synth.gaussian((batch, N), seed=batch + 1)
+    Xd, Gd = to_dev(X), to_dev(G)
+    work = torch.empty(fg.fft_filter_grad_h_workspace(N, batch) // 8, dtype=torch.complex64,
+                       device="cuda")
+    st = torch.cuda.current_stream()
+    out = []
+    for _ in range(2):
+        gH = torch.empty(N, dtype=torch.complex64, device="cuda")
+        fg.fft_filter_grad_h(Xd, Gd, gH, N, batch, work, st)
+        out.append(to_host(gH))
+    assert np.array_equal(out[0].view(np.uint32), out[1].view(np.uint32))
+    terms = np.conj(X.astype(np.complex128)) * G.astype(np.complex128)
+    want = terms.sum(0)
+    scale = np.abs(terms).sum(0)
+    assert (np.abs(out[0] - want) / scale).max() <= 1e-6
