@@ -734,7 +734,7 @@ def run_profile_case(args):
     st = torch.cuda.current_stream()
     if kind == "plan":
         cfg = json.loads(args.profile_config) if args.profile_config else None
-        p = fg.Plan(N, batch, fg.FFT_FORWARD, flags=args.profile_flags, config=cfg)
+        p = fg.Plan(N, batch, args.profile_direction, flags=args.profile_flags, config=cfg)
         for _ in range(3):
             p(x, out=y)
         info = p.info()
@@ -793,6 +793,8 @@ def main():
     ap.add_argument("--profile-case", type=int, default=0,
                     help="run one N of the sweep three times (for ncu) and exit")
     ap.add_argument("--profile-flags", type=int, default=0)
+    ap.add_argument("--profile-direction", type=int, default=-1, choices=[-1, 1],
+                    help="direction of the profiled plan (kind plan)")
     ap.add_argument("--profile-kind", default="plan",
                     choices=["plan", "tc", "filter_fwd", "filter_bwd", "ragged"])
     ap.add_argument("--profile-config", type=str, default="",

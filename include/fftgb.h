@@ -302,7 +302,11 @@ fft_status_t fft_filter_grad_h(const void *X, const void *G, void *grad_H, int N
  *   Free with fft_destroy.
  * fft_filter_forward: y = IFFT(FFT(x) * H) (conj_h = 1: * conj(H)), inverse
  *   scaled by 1/N; if X_save is non-NULL it also receives FFT(x) (needed by
- *   the backward).  x, y, X_save: batch*N float2; H: N float2.
+ *   the backward).  x, y, X_save: batch*N float2; H: N float2.  y may equal
+ *   x; X_save may not overlap x or y (FFT_ERR_INVALID_VALUE).  N <= 4096:
+ *   one kernel, one HBM round trip per row; N >= 8192: the spectrum kernel
+ *   (into X_save, else into y) and the multiply-and-inverse kernel, one
+ *   more pass (a single kernel holding both 32-point transforms spills).
  * fft_filter_backward: with g_y = dL/dy (PyTorch convention),
  *   grad_x = IFFT(FFT(g_y) * conj(H)) = F^H(conj(H) * g_z), g_z = FFT(g_y)/N,
  *   grad_H = sum_rows conj(X_saved) * g_z  (sums over 32-row chunks in row

@@ -137,11 +137,15 @@ static FilterKernel make_kernel() {
   return k;
 }
 
-// The three kernels of one N share a radix schedule (and its twiddle
-// tables): 32 points per thread from 8192 on (three passes, like the plain
-// transform's built-in), 16 below.
+// The kernels of one N share a radix schedule (and its twiddle tables): 32
+// points per thread from 8192 on (three passes, like the plain transform's
+// built-in), 16 below.  With 32 points both transforms of FM_FWD do not fit
+// the register budget (~0.8-1 KiB of spills per thread, written back to
+// DRAM), so from 8192 on the forward runs as FM_SPEC into the saved spectrum
+// (or into y) and FM_MULINV from there: one more HBM pass, no spills, and
+// measured faster.
 struct FilterVariant {
-  FilterKernel fwd, spec, mulinv;
+  FilterKernel fwd, spec, mulinv;  // fwd.fn == nullptr: the two-kernel forward
   KernelEntry sched;
 };
 
@@ -149,7 +153,8 @@ template <int N, int P, int TB, int... Rs>
 static FilterVariant variant() {
   using SC = Sched<Rs...>;
   FilterVariant v;
-  v.fwd = make_kernel<N, P, TB, SC, FM_FWD>();
+  if constexpr (P < 32) v.fwd = make_kernel<N, P, TB, SC, FM_FWD>();
+  else v.fwd = FilterKernel{nullptr, 0, 0, 0};
   v.spec = make_kernel<N, P, TB, SC, FM_SPEC>();
   v.mulinv = make_kernel<N, P, TB, SC, FM_MULINV>();
   v.sched = KernelEntry{};
@@ -222,7 +227,7 @@ fft_status_t fft_filter_plan(fft_plan_t *out, int N, int64_t batch) {
   }
   cudaMemset(pl->d_status, 0, sizeof(int));
   for (const FilterKernel *k : {&v.fwd, &v.spec, &v.mulinv}) {
-    if (k->smem > 48 * 1024 &&
+    if (k->fn && k->smem > 48 * 1024 &&
         cudaFuncSetAttribute(k->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k->smem) !=
             cudaSuccess)
       return fail(FFT_ERR_CUDA);
@@ -262,6 +267,7 @@ fft_status_t fft_filter_forward(fft_plan_t plan, const void *x, const void *H, v
   fft_plan_impl *pl = &plan->impl;
   FilterState *f = (FilterState *)pl->filter;
   if (pl->batch == 0) return FFT_OK;
+  cudaStream_t st = (cudaStream_t)stream;
   FilterArgs a{};
   a.in = (const float2 *)x;
   a.out = (float2 *)y;
@@ -271,7 +277,25 @@ fft_status_t fft_filter_forward(fft_plan_t plan, const void *x, const void *H, v
   a.batch = pl->batch;
   a.conj_h = conj_h ? 1 : 0;
   a.scale = 1.0f / (float)pl->N;
-  return filter_launch(f->v.fwd, a, (cudaStream_t)stream);
+  if (f->v.fwd.fn) return filter_launch(f->v.fwd, a, st);
+  // two kernels: F x into X_save (or y), then y = G (F x * H) from there
+  const int64_t bytes = (int64_t)sizeof(float2) * pl->N * pl->batch;
+  if (X_save) {
+    const char *p = (const char *)X_save;
+    for (const void *o : {x, (const void *)y}) {
+      const char *q = (const char *)o;
+      if (p < q + bytes && q < p + bytes) return FFT_ERR_INVALID_VALUE;
+    }
+  }
+  float2 *spec = X_save ? (float2 *)X_save : (float2 *)y;
+  a.out = spec;
+  a.x_save = nullptr;
+  a.scale = 1.0f;
+  if ((s = filter_launch(f->v.spec, a, st)) != FFT_OK) return s;
+  a.in = spec;
+  a.out = (float2 *)y;
+  a.scale = 1.0f / (float)pl->N;
+  return filter_launch(f->v.mulinv, a, st);
 }
 
 fft_status_t fft_filter_backward(fft_plan_t plan, const void *g_y, const void *H,

@@ -385,9 +385,9 @@ class _FusedSpectralFilterFn(torch.autograd.Function):
                 gH if ctx.needs_input_grad[1] else None)
 
 
-# Largest N at which the fused kernels measured faster than the separate ones
-# on GB300 (forward with the saved spectrum plus backward): every supported N
-# (at 16384 the fused forward alone is ~5 % slower, its backward ~10 % faster).
+# Largest N at which the filter plan's kernels measured faster than separate
+# transforms and multiplies on GB300 (forward with the saved spectrum plus
+# backward): every supported N.
 FUSED_MAX_N = 16384
 
 
