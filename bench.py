@@ -643,16 +643,18 @@ def bench_columns(fg, torch, dev):
 
 
 def bench_large_n(fg, torch, dev):
-    """N = 2^15..2^20 (beyond one CTA: 2-CTA clusters at 2^15, the two-phase
-    four-step above, and the four-step forced at 2^15 for comparison), 2^25
-    points per call, forward, default plans."""
+    """N = 2^15..2^20 (beyond one CTA: the two-phase four-step; and 2^15 on
+    2-CTA clusters for comparison), 2^25 points per call, forward."""
     out = {}
     x = torch.randn(POINTS, dtype=torch.complex64, device=dev)
     y = torch.empty_like(x)
-    for key in [str(1 << e) for e in range(15, 21)] + ["32768_fourstep"]:
+    for key in [str(1 << e) for e in range(15, 21)] + ["32768_cluster2"]:
         N = int(key.split("_")[0])
-        flags = fg.FFT_FLAG_FORCE_FOURSTEP if key.endswith("fourstep") else 0
-        p = fg.Plan(N, POINTS // N, fg.FFT_FORWARD, device=dev, flags=flags)
+        cfg = None
+        if key.endswith("cluster2"):
+            cfg = next(c for c in fg.fft_list_configs(N)
+                       if c["cluster_split"] == 2 and c["twiddle_mode"] == 1)
+        p = fg.Plan(N, POINTS // N, fg.FFT_FORWARD, device=dev, config=cfg)
         for _ in range(3):
             p(x, out=y)
         torch.cuda.synchronize()

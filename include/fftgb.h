@@ -143,14 +143,12 @@ const char *fft_status_string(fft_status_t status);
 
 /*
  * fft_plan — plan `batch` transforms of length N in one direction.
- * N: power of two, 2 <= N <= 2^20.  Up to 16384 a row fits one CTA.  At
- * 32768 a row runs on a 2-CTA thread-block cluster (two 16384-point halves
- * combined through distributed shared memory, one HBM pass; the plan's info
- * reports path FFT_PATH_SINGLE_CTA with cluster_split 2).  Above that the
- * two-phase four-step runs (N = n1 * n2 with a phase-1 length n2 <= 256 and
- * a phase-2 length n1 <= 4096; its intermediate doubles the HBM traffic);
- * FFT_FLAG_FORCE_FOURSTEP selects it at 32768 too.  batch >= 0 (0 makes a
- * valid plan whose
+ * N: power of two, 2 <= N <= 2^20.  Up to 16384 a row fits one CTA; above
+ * that the two-phase four-step runs (N = n1 * n2 with a phase-1 length
+ * n2 <= 256 and a phase-2 length n1 <= 4096; its intermediate doubles the
+ * HBM traffic).  Rows on thread-block clusters (cluster_split in
+ * fft_config_t, N = 8192 .. 65536) are selectable through fft_plan_config.
+ * batch >= 0 (0 makes a valid plan whose
  * exec does nothing).  direction: FFT_FORWARD or FFT_INVERSE.
  * Allocates and fills the plan's twiddle tables on the current device
  * (generated in FP64 on the GPU, rounded to FP32) and synchronises once.

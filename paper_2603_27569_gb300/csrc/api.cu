@@ -3,11 +3,12 @@
 // Planning follows the synthesis rules of the paper (Sec. IV-D) re-derived
 // for GB300: a transform whose N points fit one CTA's shared memory (every N
 // up to 16384 = 128 KiB, within the 227 KiB a CTA may use) runs as a
-// single-CTA Stockham kernel; N = 32768 runs on 2-CTA clusters (cluster.cuh,
-// the four-step with N1 = 2 in one HBM pass); the two-phase four-step path
-// (Sec. IV-B, Eq. 3) splits N = N1 N2 into column FFTs plus twiddle, then row
-// FFTs, through a device intermediate.  The autotuner's cache may override
-// the choice per (N, direction, precision) for N <= 16384.
+// single-CTA Stockham kernel; the two-phase four-step path (Sec. IV-B, Eq. 3)
+// splits N = N1 N2 into column FFTs plus twiddle, then row FFTs, through a
+// device intermediate; cluster-split rows (cluster.cuh, the four-step with
+// N1 = K in one HBM pass) are selectable configurations.  The autotuner's
+// cache may override the choice per (N, direction, precision) for
+// N <= 16384.
 //
 // Twiddle tables (Sec. V-A/V-B compute them with a sincos chain; here they are
 // precomputed once per plan): every entry W_M^e = exp(-2 pi i e / M) is

@@ -83,7 +83,8 @@ def test_single_row_in_place_and_determinism(N, cfg):
 
 def test_empty_batch_and_closed_forms():
     N = 32768
-    plan = fg.Plan(N, 0, fg.FFT_FORWARD)
+    cfg = next(c for c in fg.fft_list_configs(N) if c["cluster_split"] == 2)
+    plan = fg.Plan(N, 0, fg.FFT_FORWARD, config=cfg)
     assert plan.info()["cluster_split"] == 2
     assert fg.lib().fft_exec(plan.handle, None, None, None) == 0   # nothing to do
     plan.close()
@@ -91,7 +92,7 @@ def test_empty_batch_and_closed_forms():
     x = np.zeros((2, N), np.complex64)
     x[0, 0] = 1
     x[1, :] = 1
-    plan = fg.Plan(N, 2, fg.FFT_FORWARD)
+    plan = fg.Plan(N, 2, fg.FFT_FORWARD, config=cfg)
     y = to_host(plan(to_dev(x)))
     plan.close()
     assert np.array_equal(y[0], np.ones(N, np.complex64))

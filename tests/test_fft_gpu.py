@@ -273,17 +273,14 @@ def test_host_buffer_exec_matches_device_exec(N, flags):
 @pytest.mark.parametrize("N", [1 << e for e in range(15, 21)])
 @pytest.mark.parametrize("direction", [fg.FFT_FORWARD, fg.FFT_INVERSE])
 def test_beyond_one_cta(N, direction):
-    # N > 16384: 2-CTA clusters at 32768, else the two-phase four-step
-    # (phase 1 <= 256 points, phase 2 <= 4096); the four-step forced at every
-    # N; every listed configuration, ragged CTA tail included
+    # N > 16384: the two-phase four-step (phase 1 <= 256 points, phase 2 <=
+    # 4096), also forced; every listed configuration (four-step splits and
+    # cluster rows), ragged CTA tail included
     cfgs = fg.fft_list_configs(N)
     assert cfgs
     x = synth.gaussian((3, N), seed=N)
     y, info = run(x, direction)
-    if N == 32768:
-        assert info["path"] == fg.FFT_PATH_SINGLE_CTA and info["cluster_split"] == 2
-    else:
-        assert info["path"] == fg.FFT_PATH_FOURSTEP and info["n1"] * info["n2"] == N
+    assert info["path"] == fg.FFT_PATH_FOURSTEP and info["n1"] * info["n2"] == N
     check(x, y, direction)
     y, info = run(x, direction, flags=fg.FFT_FLAG_FORCE_FOURSTEP)
     assert info["path"] == fg.FFT_PATH_FOURSTEP and info["n1"] * info["n2"] == N
