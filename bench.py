@@ -206,9 +206,14 @@ def run_reference(args):
         v, desc = oracle_sample(budget, nthreads)
         vals.append(v)
     value = statistics.median(vals)
+    # one full step of the sweep (every N, fwd + inv, 2^25 points each) at
+    # the sampled rate: the oracle is timed on a bounded sample, not on it
+    step_flops = sum(2 * flops(N, POINTS // N) for N in SIZES)
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GFLOPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(step_flops / (value * 1e9) * 1e3, 1),
+        "ms_per_step_note": "extrapolated from the sampled rate to one full sweep step",
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "points_per_call": POINTS,
                                         "sizes": SIZES},
