@@ -2,20 +2,26 @@
 // persistent launch (paper Sec. II-D: radar workloads are batches of 1-D FFTs
 // of 2^10..2^14 points; here a batch may mix them).
 //
-// Launch shape: one 1024-thread CTA per SM with 128 KiB of shared memory.
+// Two persistent launches, one CTA per SM each, 128 KiB of shared memory.
 // Work is cut into units and taken longest-first (LPT order) through three
 // device counters, one per size class:
-//   class A  N = 16384: one row per unit, the whole CTA (barrier: CTA);
-//   class B  N = 8192:  one row per unit, each half of the CTA (512 threads,
-//                       64 KiB) claims its own units (barrier: named, per half);
-//   class C  N <= 4096: 4096 points per unit (4096 / N rows of one (N,
-//                       direction)), each quarter of the CTA (256 threads,
-//                       32 KiB) claims its own units (barrier: named, per quarter).
-// Every thread keeps 16 points in registers (radix-16 passes with a radix-2/4/8
-// tail, the single-CTA Stockham passes); a quarter therefore behaves like one
-// 256-thread CTA of the plain kernel, so small transforms keep four
-// independent barrier domains per SM.  A CTA moves A -> B -> C once, never
-// back, so no class waits for another.
+//   launch 1, 512-thread CTAs, 32 points per thread (the plain transform's
+//   built-in schedules for these sizes; 512 threads leave the 128 registers
+//   per thread they need):
+//     class A  N = 16384: one row per unit, the whole CTA (barrier: CTA);
+//     class B  N = 8192:  one row per unit, each half of the CTA (256
+//                         threads, 64 KiB) claims its own units (named
+//                         barrier per half);
+//   launch 2, 1024-thread CTAs, 16 points per thread (radix-16 passes with a
+//   radix-2/4/8 tail):
+//     class C  N <= 4096: 4096 points per unit (4096 / N rows of one (N,
+//                         direction)), each quarter of the CTA (256 threads,
+//                         32 KiB) claims its own units (named barrier per
+//                         quarter); a quarter behaves like one 256-thread CTA
+//                         of the plain kernel, and four barrier domains per
+//                         SM keep the small transforms' phases overlapped.
+// In launch 1 a CTA moves A -> B once, never back, so no class waits for
+// another.
 //
 // The counter reset and the kernel are captured once per (in, out) pair into
 // a CUDA graph that each fft_exec replays on the caller's stream.
@@ -44,8 +50,6 @@ struct RaggedUnit {
 
 constexpr int kRagMinLog2 = 4, kRagMaxLog2 = 14;
 constexpr int kRagSizes = kRagMaxLog2 - kRagMinLog2 + 1;
-constexpr int kRagThreads = 1024;
-constexpr int kRagP = 16;
 constexpr size_t kRagSmem = sizeof(float2) * 16384;
 
 struct RaggedArgs {
@@ -60,26 +64,53 @@ struct RaggedArgs {
   int unnormalized;   // inverse without 1/N
 };
 
-// Radix schedules with 16 points per thread.
-template <int N> struct RagSched;
-template <> struct RagSched<16> { using T = Sched<16>; };
-template <> struct RagSched<32> { using T = Sched<16, 2>; };
-template <> struct RagSched<64> { using T = Sched<16, 4>; };
-template <> struct RagSched<128> { using T = Sched<16, 8>; };
-template <> struct RagSched<256> { using T = Sched<16, 16>; };
-template <> struct RagSched<512> { using T = Sched<16, 16, 2>; };
-template <> struct RagSched<1024> { using T = Sched<16, 16, 4>; };
-template <> struct RagSched<2048> { using T = Sched<16, 16, 8>; };
-template <> struct RagSched<4096> { using T = Sched<16, 16, 16>; };
-template <> struct RagSched<8192> { using T = Sched<16, 16, 16, 2>; };
-template <> struct RagSched<16384> { using T = Sched<16, 16, 16, 4>; };
+// Radix schedules (P points per thread, twiddle mode TWM).  rag_radices()
+// below lists the same schedules for the host's twiddle tables.
+template <int N> struct RagSched { static constexpr int P = 16, TWM = 0; };
+template <> struct RagSched<16> : RagSched<0> { using T = Sched<16>; };
+template <> struct RagSched<32> : RagSched<0> { using T = Sched<16, 2>; };
+template <> struct RagSched<64> : RagSched<0> { using T = Sched<16, 4>; };
+template <> struct RagSched<128> : RagSched<0> { using T = Sched<16, 8>; };
+template <> struct RagSched<256> : RagSched<0> { using T = Sched<16, 16>; };
+template <> struct RagSched<512> : RagSched<0> { using T = Sched<16, 16, 2>; };
+template <> struct RagSched<1024> : RagSched<0> { using T = Sched<16, 16, 4>; };
+template <> struct RagSched<2048> : RagSched<0> { using T = Sched<16, 16, 8>; };
+template <> struct RagSched<4096> : RagSched<0> { using T = Sched<16, 16, 16>; };
+template <> struct RagSched<8192> {
+  using T = Sched<32, 16, 16>;
+  static constexpr int P = 32, TWM = 0;
+};
+template <> struct RagSched<16384> {
+  using T = Sched<32, 32, 16>;
+  static constexpr int P = 32, TWM = 1;
+};
+
+// Radices of the schedule for N = 2^e (host copy of RagSched); returns the
+// number of passes.
+static int rag_radices(int e, int *rad) {
+  if (e == 14) {
+    rad[0] = 32, rad[1] = 32, rad[2] = 16;
+    return 3;
+  }
+  if (e == 13) {
+    rad[0] = 32, rad[1] = 16, rad[2] = 16;
+    return 3;
+  }
+  int np = 0, rest = 1 << e;
+  while (rest > 1) {
+    const int rr = rest >= 16 ? 16 : rest;
+    rad[np++] = rr;
+    rest /= rr;
+  }
+  return np;
+}
 
 // One unit by a group of GT threads (gtid = thread index in the group).
 template <int N, int D, int GT, class BR>
 __device__ __forceinline__ void rag_unit(const RaggedArgs &a, const RaggedUnit &u, int gtid,
                                          float2 *sm, const BR &br) {
   using SC = typename RagSched<N>::T;
-  constexpr int P = kRagP;
+  constexpr int P = RagSched<N>::P;
   constexpr int T = N / P;
   static_assert(GT % T == 0, "group must hold whole rows");
   const int b = gtid / T;
@@ -97,8 +128,8 @@ __device__ __forceinline__ void rag_unit(const RaggedArgs &a, const RaggedUnit &
     for (int m = 0; m < P; ++m) v[m] = make_float2(0.f, 0.f);
   }
   const float2 *tw = a.tw + a.tw_off[ilog2(N) - kRagMinLog2];
-  run_passes<N, P, D, SC, 0, SwizzledRow, 0, BR>(v, lt, sm + (size_t)b * N, tw, SwizzledRow{},
-                                                 br);
+  run_passes<N, P, D, SC, 0, SwizzledRow, RagSched<N>::TWM, BR>(v, lt, sm + (size_t)b * N, tw,
+                                                                 SwizzledRow{}, br);
   if (active) {
     const float s = (D > 0 && !a.unnormalized) ? 1.0f / (float)N : 1.0f;
     float2 *dst = a.out + d.out_off;
@@ -108,7 +139,9 @@ __device__ __forceinline__ void rag_unit(const RaggedArgs &a, const RaggedUnit &
   br.sync();  // the group's buffer is reused by its next unit
 }
 
-template <int GT, class BR>
+// Sizes by class: LARGE (launch 1): 8192 on 256-thread halves, 16384 on the
+// 512-thread CTA; otherwise (launch 2) N <= 4096 on 256-thread quarters.
+template <int GT, bool LARGE, class BR>
 __device__ void rag_dispatch(const RaggedArgs &a, const RaggedUnit &u, int gtid, float2 *sm,
                              const BR &br) {
 #define FFTGB_RAG_CASE(L)                                                        \
@@ -116,7 +149,7 @@ __device__ void rag_dispatch(const RaggedArgs &a, const RaggedUnit &u, int gtid,
     if (u.dir < 0) rag_unit<(1 << L), -1, GT, BR>(a, u, gtid, sm, br);           \
     else rag_unit<(1 << L), +1, GT, BR>(a, u, gtid, sm, br);                     \
     break;
-  if constexpr (GT == 256) {
+  if constexpr (!LARGE) {
     switch (u.log2n) {
       FFTGB_RAG_CASE(4)
       FFTGB_RAG_CASE(5)
@@ -129,7 +162,7 @@ __device__ void rag_dispatch(const RaggedArgs &a, const RaggedUnit &u, int gtid,
       FFTGB_RAG_CASE(12)
       default: break;
     }
-  } else if constexpr (GT == 512) {
+  } else if constexpr (GT == 256) {
     switch (u.log2n) {
       FFTGB_RAG_CASE(13)
       default: break;
@@ -143,46 +176,47 @@ __device__ void rag_dispatch(const RaggedArgs &a, const RaggedUnit &u, int gtid,
 #undef FFTGB_RAG_CASE
 }
 
-__global__ void __launch_bounds__(kRagThreads) ragged_kernel(RaggedArgs a) {
+// Launch 1: classes A (whole 512-thread CTA) and B (256-thread halves).
+__global__ void __launch_bounds__(512, 1) ragged_large_kernel(RaggedArgs a) {
   extern __shared__ __align__(128) float2 smem[];
-  __shared__ int claim[7];
+  __shared__ int claim[3];
   const int tid = threadIdx.x;
-  // class A: the whole CTA
   while (true) {
     if (tid == 0) claim[0] = (int)atomicAdd(a.counters + 0, 1u);
     __syncthreads();
     const int u = claim[0];
     __syncthreads();
     if (u >= a.nA) break;
-    rag_dispatch<1024>(a, a.units[u], tid, smem, CtaBarrier{});
+    rag_dispatch<512, true>(a, a.units[u], tid, smem, CtaBarrier{});
   }
-  // class B: two halves
-  {
-    const int h = tid / 512, htid = tid - h * 512;
-    const NamedBarrier br{1 + h, 512};
-    float2 *sm = smem + (size_t)h * 8192;
-    while (true) {
-      if (htid == 0) claim[1 + h] = (int)atomicAdd(a.counters + 1, 1u);
-      br.sync();
-      const int u = claim[1 + h];
-      br.sync();
-      if (u >= a.nB) break;
-      rag_dispatch<512>(a, a.units[a.nA + u], htid, sm, br);
-    }
+  const int h = tid / 256, htid = tid - h * 256;
+  const NamedBarrier br{1 + h, 256};
+  float2 *sm = smem + (size_t)h * 8192;
+  while (true) {
+    if (htid == 0) claim[1 + h] = (int)atomicAdd(a.counters + 1, 1u);
+    br.sync();
+    const int u = claim[1 + h];
+    br.sync();
+    if (u >= a.nB) break;
+    rag_dispatch<256, true>(a, a.units[a.nA + u], htid, sm, br);
   }
-  // class C: four quarters
-  {
-    const int q = tid / 256, qtid = tid - q * 256;
-    const NamedBarrier br{3 + q, 256};
-    float2 *sm = smem + (size_t)q * 4096;
-    while (true) {
-      if (qtid == 0) claim[3 + q] = (int)atomicAdd(a.counters + 2, 1u);
-      br.sync();
-      const int u = claim[3 + q];
-      br.sync();
-      if (u >= a.nC) break;
-      rag_dispatch<256>(a, a.units[a.nA + a.nB + u], qtid, sm, br);
-    }
+}
+
+// Launch 2: class C on four 256-thread quarters.
+__global__ void __launch_bounds__(1024) ragged_small_kernel(RaggedArgs a) {
+  extern __shared__ __align__(128) float2 smem[];
+  __shared__ int claim[4];
+  const int tid = threadIdx.x;
+  const int q = tid / 256, qtid = tid - q * 256;
+  const NamedBarrier br{1 + q, 256};
+  float2 *sm = smem + (size_t)q * 4096;
+  while (true) {
+    if (qtid == 0) claim[q] = (int)atomicAdd(a.counters + 2, 1u);
+    br.sync();
+    const int u = claim[q];
+    br.sync();
+    if (u >= a.nC) break;
+    rag_dispatch<256, false>(a, a.units[a.nA + a.nB + u], qtid, sm, br);
   }
 }
 
@@ -233,8 +267,12 @@ static fft_status_t capture(RaggedState *r, const float2 *in, float2 *out) {
   cudaMemsetAsync(r->d_counters, 0, 3 * sizeof(unsigned), r->cap);
   RaggedArgs a = r->args;
   void *args[] = {&a};
-  cudaLaunchKernel((const void *)ragged_kernel, dim3(r->grid), dim3(kRagThreads), args,
-                   kRagSmem, r->cap);
+  if (a.nA + a.nB > 0)
+    cudaLaunchKernel((const void *)ragged_large_kernel, dim3(r->grid), dim3(512), args, kRagSmem,
+                     r->cap);
+  if (a.nC > 0)
+    cudaLaunchKernel((const void *)ragged_small_kernel, dim3(r->grid), dim3(1024), args,
+                     kRagSmem, r->cap);
   if (cudaStreamEndCapture(r->cap, &g) != cudaSuccess || !g) {
     cudaGetLastError();
     return FFT_ERR_CUDA;
@@ -345,13 +383,8 @@ extern "C" fft_status_t fft_ragged_plan(fft_plan_t *out, int count, const int *N
   int64_t total = 0;
   for (int e = kRagMinLog2; e <= kRagMaxLog2; ++e) {
     tw_off[e - kRagMinLog2] = total;
-    int rad[4] = {16, 0, 0, 0};
-    int np = 1, rest = (1 << e) / 16;
-    while (rest > 1) {
-      const int rr = rest >= 16 ? 16 : rest;
-      rad[np++] = rr;
-      rest /= rr;
-    }
+    int rad[8] = {0};
+    const int np = rag_radices(e, rad);
     int p = rad[0];
     for (int k = 1; k < np; ++k) {
       passes.push_back({p, rad[k]});
@@ -383,10 +416,10 @@ extern "C" fft_status_t fft_ragged_plan(fft_plan_t *out, int count, const int *N
   }
   if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
     return fail(FFT_ERR_CUDA);
-  if (cudaFuncSetAttribute((const void *)ragged_kernel,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRagSmem) !=
-      cudaSuccess)
-    return fail(FFT_ERR_CUDA);
+  for (const void *fn : {(const void *)ragged_large_kernel, (const void *)ragged_small_kernel})
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRagSmem) !=
+        cudaSuccess)
+      return fail(FFT_ERR_CUDA);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device);
   r->grid = std::max(1, std::min<int>(sms, (int)units.size()));
