@@ -60,7 +60,7 @@ __global__ void __cluster_dims__(K, 1, 1)
   cg::cluster_group cl = cg::this_cluster();
   const int r = (int)cl.block_rank();
   const long long c0 = blockIdx.x / K, ncl = gridDim.x / K;
-  extern __shared__ __align__(16) float2 smem[];
+  extern __shared__ __align__(128) float2 smem[];
   const int lt = threadIdx.x;
   // Scatter targets of this thread: pair j = lt + m T holds elements
   // e = r H + 2 j and e + 1; with K | H and K | 2 T they go to CTAs

@@ -48,7 +48,7 @@ column_kernel(ColumnArgs args) {
   static_assert(P % SC::max_radix() == 0, "every radix must divide P");
   constexpr int T = L / P;
   constexpr int NT = C * T;
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(128) float2 smem[];
   const int c = threadIdx.x % C;
   const int lt = threadIdx.x / C;
   const int tiles_per_mat = args.ncols / C;

@@ -55,7 +55,7 @@ template <int N, int P, int TB, class SC, int MODE>
 __global__ void __launch_bounds__(TB *(N / P), (65536 / (TB * (N / P) * 128)) > 0 ? 65536 / (TB * (N / P) * 128) : 1)
 filter_kernel(FilterArgs a) {
   constexpr int T = N / P;
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(128) float2 smem[];
   const int b = threadIdx.x / T;
   const int lt = threadIdx.x - b * T;
   float2 *buf = smem + b * N;

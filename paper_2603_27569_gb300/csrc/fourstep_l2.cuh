@@ -95,7 +95,7 @@ fourstep_l2_kernel(FourstepL2Args a) {
   constexpr int NT = C * T;
   constexpr int GROUPS = L / C;  // column tiles per row and phase
   static_assert(NT >= 64, "two warps needed (claims and completions)");
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(128) float2 smem[];
   __shared__ long long s_item[2];
   __shared__ int s_ok;
   const int c = threadIdx.x % C;

@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(TB *(N / P))
 stockham_half_kernel(HalfArgs args) {
   static_assert(SC::product() == N, "radix schedule must multiply to N");
   constexpr int T = N / P;
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(128) float2 smem[];
   const int b = threadIdx.x / T;
   const int lt = threadIdx.x - b * T;
   float2 *buf = smem + b * N;

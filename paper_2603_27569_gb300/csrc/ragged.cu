@@ -334,7 +334,6 @@ extern "C" fft_status_t fft_ragged_plan(fft_plan_t *out, int count, const int *N
   pl->ragged = r;
   r->count = count;
   cudaGetDevice(&pl->device);
-  fft_status_t s = FFT_OK;
   auto fail = [&](fft_status_t e) {
     ragged_free(r);
     pl->ragged = nullptr;
@@ -435,7 +434,6 @@ extern "C" fft_status_t fft_ragged_plan(fft_plan_t *out, int count, const int *N
   a.tw = r->d_tw;
   for (int i = 0; i < kRagSizes; ++i) a.tw_off[i] = tw_off[i];
   a.unnormalized = (flags & FFT_FLAG_UNNORMALIZED_INVERSE) ? 1 : 0;
-  (void)s;
   *out = h;
   return FFT_OK;
 }

@@ -327,7 +327,7 @@ stockham_kernel(StockhamArgs args) {
   static_assert(SC::product() == N, "radix schedule must multiply to N");
   static_assert(P % SC::max_radix() == 0, "every radix must divide P");
   constexpr int T = N / P;
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(128) float2 smem[];
   const int b = threadIdx.x / T;
   const int lt = threadIdx.x - b * T;
   float2 *buf = smem + b * N;
