@@ -2,9 +2,9 @@
 // persistent launch (paper Sec. II-D: radar workloads are batches of 1-D FFTs
 // of 2^10..2^14 points; here a batch may mix them).
 //
-// Two persistent launches, one CTA per SM each, 128 KiB of shared memory.
-// Work is cut into units and taken longest-first (LPT order) through three
-// device counters, one per size class:
+// Two launches.  Work is cut into units, longest first (LPT order); the
+// large rows are claimed through device counters by a persistent grid (one
+// CTA per SM, 128 KiB of shared memory), the small units each get a CTA:
 //   launch 1, 512-thread CTAs, 32 points per thread (the plain transform's
 //   built-in schedules for these sizes; 512 threads leave the 128 registers
 //   per thread they need):
@@ -12,14 +12,13 @@
 //     class B  N = 8192:  one row per unit, each half of the CTA (256
 //                         threads, 64 KiB) claims its own units (named
 //                         barrier per half);
-//   launch 2, 1024-thread CTAs, 16 points per thread (radix-16 passes with a
-//   radix-2/4/8 tail):
+//   launch 2, one 256-thread CTA (32 KiB) per unit, 16 points per thread
+//   (radix-16 passes with a radix-2/4/8 tail):
 //     class C  N <= 4096: 4096 points per unit (4096 / N rows of one (N,
-//                         direction)), each quarter of the CTA (256 threads,
-//                         32 KiB) claims its own units (named barrier per
-//                         quarter); a quarter behaves like one 256-thread CTA
-//                         of the plain kernel, and four barrier domains per
-//                         SM keep the small transforms' phases overlapped.
+//                         direction)), units in longest-first order; a CTA
+//                         behaves like one 256-thread CTA of the plain
+//                         kernel (a persistent grid of claiming CTAs measured
+//                         slower: its CTAs run in lockstep).
 // In launch 1 a CTA moves A -> B once, never back, so no class waits for
 // another.
 //
@@ -202,22 +201,12 @@ __global__ void __launch_bounds__(512, 1) ragged_large_kernel(RaggedArgs a) {
   }
 }
 
-// Launch 2: class C on four 256-thread quarters.
-__global__ void __launch_bounds__(1024) ragged_small_kernel(RaggedArgs a) {
+// Launch 2: class C, one 256-thread CTA (32 KiB) per unit, in the units'
+// longest-first order; the hardware scheduler keeps several units per SM
+// in flight and staggers their phases.
+__global__ void __launch_bounds__(256) ragged_small_kernel(RaggedArgs a) {
   extern __shared__ __align__(128) float2 smem[];
-  __shared__ int claim[4];
-  const int tid = threadIdx.x;
-  const int q = tid / 256, qtid = tid - q * 256;
-  const NamedBarrier br{1 + q, 256};
-  float2 *sm = smem + (size_t)q * 4096;
-  while (true) {
-    if (qtid == 0) claim[q] = (int)atomicAdd(a.counters + 2, 1u);
-    br.sync();
-    const int u = claim[q];
-    br.sync();
-    if (u >= a.nC) break;
-    rag_dispatch<256, false>(a, a.units[a.nA + a.nB + u], qtid, sm, br);
-  }
+  rag_dispatch<256, false>(a, a.units[a.nA + a.nB + blockIdx.x], threadIdx.x, smem, CtaBarrier{});
 }
 
 // FP64-generated pass tables (api.cu).
@@ -271,8 +260,8 @@ static fft_status_t capture(RaggedState *r, const float2 *in, float2 *out) {
     cudaLaunchKernel((const void *)ragged_large_kernel, dim3(r->grid), dim3(512), args, kRagSmem,
                      r->cap);
   if (a.nC > 0)
-    cudaLaunchKernel((const void *)ragged_small_kernel, dim3(r->grid), dim3(1024), args,
-                     kRagSmem, r->cap);
+    cudaLaunchKernel((const void *)ragged_small_kernel, dim3((unsigned)a.nC), dim3(256), args,
+                     sizeof(float2) * 4096, r->cap);
   if (cudaStreamEndCapture(r->cap, &g) != cudaSuccess || !g) {
     cudaGetLastError();
     return FFT_ERR_CUDA;
@@ -415,10 +404,10 @@ extern "C" fft_status_t fft_ragged_plan(fft_plan_t *out, int count, const int *N
   }
   if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
     return fail(FFT_ERR_CUDA);
-  for (const void *fn : {(const void *)ragged_large_kernel, (const void *)ragged_small_kernel})
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRagSmem) !=
-        cudaSuccess)
-      return fail(FFT_ERR_CUDA);
+  if (cudaFuncSetAttribute((const void *)ragged_large_kernel,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRagSmem) !=
+      cudaSuccess)
+    return fail(FFT_ERR_CUDA);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device);
   r->grid = std::max(1, std::min<int>(sms, (int)units.size()));
