@@ -29,7 +29,7 @@ def L():
     return fg.lib()
 
 
-def test_header_declares_the_north_star_interface():
+def test_header_declares_the_plan_exec_interface():
     names = declared_functions()
     for required in ("fft_plan", "fft_exec", "fft_destroy", "fft_plan_ex", "fft_ragged_plan",
                      "fft_autotune", "fft_status_string", "fft_last_device_status"):
