@@ -66,7 +66,7 @@ typedef enum {
     FFT_ERR_ALLOC = 4,          /* device or host allocation failed            */
     FFT_ERR_CUDA = 5,           /* a CUDA runtime call failed                  */
     FFT_ERR_TIMEOUT = 6,        /* a bounded device-side wait ran out          */
-    FFT_ERR_NOT_SUPPORTED = 7   /* valid request this build does not implement */
+    FFT_ERR_NOT_SUPPORTED = 7   /* valid request the library does not implement */
 } fft_status_t;
 
 /* Plan flags (bitwise OR). */
