@@ -284,6 +284,92 @@ __device__ __forceinline__ void run_passes(float2 (&a)[P], int lt, float2 *buf,
   }
 }
 
+// Twiddle-table rows of pass S for this thread's butterflies, read ahead:
+// run_passes_early issues these loads before the barrier that precedes the
+// pass's exchange read, so their latency overlaps the barrier wait (the
+// rows do not depend on the exchanged data).  Only the rows the twiddle mode
+// reads are filled; pass_apply derives the rest.
+template <int N, int P, class SC, int S, int TWM, bool PAIRED>
+struct PassTw {
+  static constexpr int r = SC::radix[S];
+  static constexpr int p = SC::stride(S);
+  static constexpr int T = N / P;
+  static constexpr int Q = P / r;
+  float2 w[Q][r];
+  __device__ __forceinline__ void load(int lt, const float2 *__restrict__ tw) {
+    const float2 *tws = tw + SC::tw_offset(S);
+    if constexpr (PAIRED) {
+      const int k0 = bfly<T, Q, true>(lt, 0) & (p - 1);
+#pragma unroll
+      for (int j = 1; j < r; ++j)
+        if (TWM == 0 || tw_loaded<r>(j)) {
+          const float4 v = __ldg(reinterpret_cast<const float4 *>(tws + (j - 1) * p + k0));
+          w[0][j] = make_float2(v.x, v.y);
+          w[1][j] = make_float2(v.z, v.w);
+        }
+    } else {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int k = bfly<T, Q, false>(lt, q) & (p - 1);
+#pragma unroll
+        for (int j = 1; j < r; ++j)
+          if (TWM == 0 || tw_loaded<r>(j)) w[q][j] = __ldg(tws + (j - 1) * p + k);
+      }
+    }
+  }
+};
+struct NoTw {};
+
+// Pass S from read-ahead twiddle rows (S > 0) or none (S = 0): the same
+// twiddle multiplies and butterflies as pass_compute.
+template <int N, int P, int D, class SC, int S, int TWM, class PT>
+__device__ __forceinline__ void pass_apply(float2 (&a)[P], const PT &t) {
+  constexpr int r = SC::radix[S];
+  constexpr int Q = P / r;
+  if constexpr (S > 0) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      float2 w[r];
+#pragma unroll
+      for (int j = 1; j < r; ++j)
+        if (TWM == 0 || tw_loaded<r>(j)) w[j] = t.w[q][j];
+      if constexpr (TWM == 1) derive_twiddles<r>(w);
+#pragma unroll
+      for (int j = 1; j < r; ++j) a[q + j * Q] = cmul_dir<D>(a[q + j * Q], w[j]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    float2 v[r];
+#pragma unroll
+    for (int j = 0; j < r; ++j) v[j] = a[q + j * Q];
+    Dft<r, D>::run(v);
+#pragma unroll
+    for (int j = 0; j < r; ++j) a[q + j * Q] = v[j];
+  }
+}
+
+// run_passes for one row per thread group with the whole CTA as barrier
+// domain and the swizzled row layout, reading each pass's twiddle rows
+// ahead of its exchange barrier (PassTw).  hk() as in run_passes.
+template <int N, int P, int D, class SC, int S, int TWM, bool PAIR_LAST, class HK, class PT>
+__device__ __forceinline__ void run_passes_early(float2 (&a)[P], int lt, float2 *buf,
+                                                 const float2 *__restrict__ tw, const HK &hk,
+                                                 const PT &pre) {
+  pass_apply<N, P, D, SC, S, TWM>(a, pre);
+  if constexpr (S + 1 < SC::npass) {
+    constexpr bool PN = PAIR_LAST && S + 2 == SC::npass;
+    if constexpr (S > 0) __syncthreads();  // every read of the buffer is done
+    pass_write<N, P, SC, S>(a, lt, buf, SwizzledRow{});
+    PassTw<N, P, SC, S + 1, TWM, PN> next;
+    next.load(lt, tw);
+    __syncthreads();
+    if constexpr (S == 0) hk();
+    pass_read<N, P, SC, S, SwizzledRow, PN>(a, lt, buf, SwizzledRow{});
+    run_passes_early<N, P, D, SC, S + 1, TWM, PAIR_LAST>(a, lt, buf, tw, hk, next);
+  }
+}
+
 // Final-pass output index of register m (after run_passes): the last pass
 // has p = N / r, so butterfly i writes j to i + j N / r.
 template <int N, int P, class SC>
@@ -365,10 +451,12 @@ stockham_kernel(StockhamArgs args) {
     float2 *bufp = buf;
     int ltp = lt;
     asm volatile("" : "+l"(twp), "+l"(bufp), "+r"(ltp));
-    run_passes<N, P, D, SC, 0, SwizzledRow, TWM, CtaBarrier, PAIR_LAST>(
-        a, ltp, bufp, twp, SwizzledRow{}, CtaBarrier{}, [&]() {
+    run_passes_early<N, P, D, SC, 0, TWM, PAIR_LAST>(
+        a, ltp, bufp, twp,
+        [&]() {
           if (first) prefetch_next();
-        });
+        },
+        NoTw{});
     if (active) {
       float2 *dst = args.out + row * N;
       const float s = args.scale;
