@@ -1,5 +1,5 @@
-// Fused spectral filter: y = IFFT(FFT(x) * H) in one kernel per row, and its
-// backward, for the SAR range-compression layer (paper Sec. II-D; the fused
+// Fused spectral filter: y = IFFT(FFT(x) * H) in one kernel per row (two
+// from N = 8192 on, see variant()), and its backward, for the SAR range-compression layer (paper Sec. II-D; the fused
 // FFT -> matched filter -> IFFT pipeline is the paper's future work, Sec. IX-A).
 //
 // After any forward Stockham transform (stockham.cuh) thread lt holds output
@@ -10,6 +10,7 @@
 //
 //   forward   y = G (F x * H)              (conj_h: * conj(H))       FM_FWD
 //             X_save = F x                 (optional, for the backward)
+//             (N >= 8192: FM_SPEC into X_save or y, then FM_MULINV)
 //   backward  g_z = G^H g_y = F g_y / N                              FM_SPEC
 //             grad_H = sum_rows conj(X) * g_z   (fft_filter_grad_h: 32-row
 //                      chunks, then a fixed-order pairwise tree)
