@@ -125,3 +125,27 @@ def test_grad_h_reduction_both_tree_forms(batch):
     want = terms.sum(0)
     scale = np.abs(terms).sum(0)
     assert (np.abs(out[0] - want) / scale).max() <= 1e-6
+
+
+@pytest.mark.parametrize("N", [4096, 8192])
+def test_filter_plan_rejects_aliased_buffers(N):
+    # host-side checks before any launch: grad_x holds g_z between the
+    # backward's kernels, and from 8192 on X_save holds the forward's spectrum
+    rows = 3
+    plan = fg.fft_filter_plan(N, rows)
+    L = fg.lib()
+    a = torch.zeros(rows * N, dtype=torch.complex64, device="cuda")
+    b = torch.zeros_like(a)
+    c = torch.zeros_like(a)
+    H = torch.ones(N, dtype=torch.complex64, device="cuda")
+    gH = torch.empty_like(H)
+    pa, pb, pc, ph, pg = a.data_ptr(), b.data_ptr(), c.data_ptr(), H.data_ptr(), gH.data_ptr()
+    assert L.fft_filter_backward(plan, pa, ph, pb, pa, pg, None) == 2   # grad_x is g_y
+    assert L.fft_filter_backward(plan, pa, ph, pb, pb, pg, None) == 2   # grad_x is X_saved
+    assert L.fft_filter_backward(plan, pa, ph, pb, pc, pg, None) == 0
+    if N >= 8192:
+        assert L.fft_filter_forward(plan, pa, ph, pb, pa, 0, None) == 2  # X_save is x
+        assert L.fft_filter_forward(plan, pa, ph, pb, pb, 0, None) == 2  # X_save is y
+    assert L.fft_filter_forward(plan, pa, ph, pa, pc, 0, None) == 0      # y may be x
+    torch.cuda.synchronize()
+    fg.fft_destroy(plan)
