@@ -28,6 +28,9 @@
 // by exhaustive search on a model of the bank mapping so that every
 // exchange store is conflict-free, the first stage's row stores take the
 // minimum wavefronts and the global loads/stores touch the minimum sectors.
+// N = 4096 uses the unpadded 128/512 layout instead: 36 KiB per CTA fits six
+// CTAs per SM (five with padding), which measured faster than the
+// conflict-free stores.
 // N = 16384 = 16^3 * 4 ends with a radix-4 pass in registers: each thread's
 // four TMEM tiles hold the four butterflies that feed one radix-4 butterfly.
 #include <cuda_bf16.h>
@@ -72,7 +75,7 @@ struct TcCfg<256> {
 };
 template <>
 struct TcCfg<4096> {
-  static constexpr int S = 3, TAIL = 0, TB = 1, NW = 4, LBO = 144, SBO = 576, MINB = 5;
+  static constexpr int S = 3, TAIL = 0, TB = 1, NW = 4, LBO = 128, SBO = 512, MINB = 6;
   static constexpr bool PERSIST = false;
   static constexpr unsigned long long R0 = 0x76354210ull, R1 = 0x73210654ull, R2 = 0x76543102ull;
 };
