@@ -8,6 +8,12 @@
 // D is the sign of the exponent: D = -1 forward (W = e^{-2 pi i/R}), D = +1
 // inverse.  Multiplications by the constant roots W_R^k use exact special
 // cases for k*8/R integral (1, -i, W_8) and two FMUL + two FFMA otherwise.
+// Inside the radix-2 combine steps the rotation is fused into the butterfly
+// (e +- o w) in the tangent form: with w = c + i s and g the larger of |c|
+// and |s|, o w = g u where u = o rotated by the ratio of the smaller to g
+// (|ratio| <= 1), so the pair costs 2 FFMA for u and 4 FFMA for e +- g u:
+// six instructions instead of eight (four for o w, four for the add and
+// the subtract).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -38,7 +44,19 @@ __device__ __forceinline__ float2 rot90(float2 a) {
   else return make_float2(-a.y, a.x);
 }
 
-// cos(j pi / 16), j = 0..8
+// cos(j pi / 16), j = 0..8, in FP32 and in FP64 (the FP64 copy forms the
+// tangent-form ratios before their single rounding to FP32)
+struct Cos16d {
+  static constexpr double d[9] = {1.0,
+                                  0.98078528040323044913,
+                                  0.92387953251128675613,
+                                  0.83146961230254523708,
+                                  0.70710678118654752440,
+                                  0.55557023301960222474,
+                                  0.38268343236508977173,
+                                  0.19509032201612826785,
+                                  0.0};
+};
 struct Cos16 {
   static constexpr float c[9] = {1.0f,
                                  0.98078528040323044913f,
@@ -83,13 +101,6 @@ __device__ __forceinline__ float2 rot32(float2 v) {
   }
 }
 
-// v * W_R^{k} with the sign D, for R dividing 32.
-template <int R, int K, int D>
-__device__ __forceinline__ float2 rotR(float2 v) {
-  static_assert(32 % R == 0, "constant roots only for R | 32");
-  return rot32<K * (32 / R), D>(v);
-}
-
 template <int R, int D>
 struct Dft;
 
@@ -121,14 +132,46 @@ struct Dft<4, D> {
   }
 };
 
+// lo = e + o w, hi = e - o w for the constant root w = exp(D 2 pi i M / 32).
+// Multiples of pi/2 are exact swaps and sign changes; every other root uses
+// the tangent form (header): |c| >= |s|: o w = c (o.x - o.y q, o.y + o.x q),
+// q = s / c; |s| > |c|: o w = s (o.x q - o.y, o.y q + o.x), q = c / s.
+template <int M, int D>
+__device__ __forceinline__ void bfly_rot32(float2 e, float2 o, float2 &lo, float2 &hi) {
+  constexpr int m = ((M % 32) + 32) % 32;
+  if constexpr (m % 8 == 0) {
+    const float2 t = rot32<m, D>(o);
+    lo = cadd(e, t);
+    hi = csub(e, t);
+  } else {
+    constexpr int q4 = m / 8, r = m % 8;
+    // cos and sin of m pi / 16 by quadrant (as in rot32), in FP64
+    constexpr double c = (q4 == 0) ? Cos16d::d[r] : (q4 == 1) ? -Cos16d::d[8 - r]
+                       : (q4 == 2) ? -Cos16d::d[r] : Cos16d::d[8 - r];
+    constexpr double s0 = (q4 == 0) ? Cos16d::d[8 - r] : (q4 == 1) ? Cos16d::d[r]
+                        : (q4 == 2) ? -Cos16d::d[8 - r] : -Cos16d::d[r];
+    constexpr double s = (D < 0) ? -s0 : s0;
+    constexpr bool cbig = (c < 0 ? -c : c) >= (s < 0 ? -s : s);
+    constexpr float q = cbig ? (float)(s / c) : (float)(c / s);
+    constexpr float g = cbig ? (float)c : (float)s;
+    float2 u;
+    if constexpr (cbig) {
+      u = make_float2(fmaf(-o.y, q, o.x), fmaf(o.x, q, o.y));
+    } else {
+      u = make_float2(fmaf(o.x, q, -o.y), fmaf(o.y, q, o.x));
+    }
+    lo = make_float2(fmaf(u.x, g, e.x), fmaf(u.y, g, e.y));
+    hi = make_float2(fmaf(u.x, -g, e.x), fmaf(u.y, -g, e.y));
+  }
+}
+
 // Radix-2 DIT step: DFT_R from DFT_{R/2} of the even and odd samples.
 template <int R, int D, int K>
 struct Combine {
+  static_assert(32 % R == 0, "constant roots only for R | 32");
   static __device__ __forceinline__ void run(float2 (&a)[R], const float2 (&e)[R / 2],
                                              const float2 (&o)[R / 2]) {
-    float2 t = rotR<R, K, D>(o[K]);
-    a[K] = cadd(e[K], t);
-    a[K + R / 2] = csub(e[K], t);
+    bfly_rot32<K * (32 / R), D>(e[K], o[K], a[K], a[K + R / 2]);
     if constexpr (K + 1 < R / 2) Combine<R, D, K + 1>::run(a, e, o);
   }
 };
