@@ -66,66 +66,6 @@ struct StockhamArgs {
   float scale;          // applied at the final store (1 or 1/N)
 };
 
-// Is row j of a pass table loaded (twiddle mode 1) rather than derived?
-template <int r>
-__host__ __device__ constexpr bool tw_loaded(int j) {
-  return j == 1 || (r == 4 && j == 2) || (r >= 8 && j == 4) || (r == 32 && j == 16);
-}
-
-// a b and a conj(b) with their shared products formed once: 2 FMUL + 4 FFMA
-// for the two, against 2 x (FMUL + FFMA) x 2 for two separate products.
-__device__ __forceinline__ void cmul_pm(float2 a, float2 b, float2 &plus, float2 &minus) {
-  const float t = a.y * b.y, u = a.x * b.y;
-  plus = make_float2(fmaf(a.x, b.x, -t), fmaf(a.y, b.x, u));
-  minus = make_float2(fmaf(a.x, b.x, t), fmaf(a.y, b.x, -u));
-}
-
-// Twiddle mode 1: form the rows that are not read as products of rows
-// already formed, W^{(c +- d) k} = W^{c k} W^{+-d k}, the two signs of one
-// (c, d) together (cmul_pm), from rows 1, 4 (and 2 for r = 4, 16 for
-// r = 32); product depth <= 3.
-template <int r>
-__device__ __forceinline__ void derive_twiddles(float2 (&w)[r]) {
-  if constexpr (r == 4) {
-    w[3] = cmul(w[2], w[1]);
-  } else if constexpr (r == 8) {
-    w[2] = cmul(w[1], w[1]);
-    cmul_pm(w[4], w[1], w[5], w[3]);
-    w[6] = cmul(w[4], w[2]);
-    w[7] = cmul(w[4], w[3]);
-  } else if constexpr (r == 16) {
-    w[2] = cmul(w[1], w[1]);
-    w[8] = cmul(w[4], w[4]);
-    cmul_pm(w[4], w[1], w[5], w[3]);
-    cmul_pm(w[8], w[1], w[9], w[7]);
-    cmul_pm(w[8], w[2], w[10], w[6]);
-    w[12] = cmul(w[8], w[4]);
-    cmul_pm(w[12], w[1], w[13], w[11]);
-    w[14] = cmul(w[12], w[2]);
-    w[15] = cmul(w[12], w[3]);
-  } else if constexpr (r == 32) {
-    w[2] = cmul(w[1], w[1]);
-    w[8] = cmul(w[4], w[4]);
-    cmul_pm(w[16], w[4], w[20], w[12]);
-    w[24] = cmul(w[16], w[8]);
-    w[28] = cmul(w[16], w[12]);
-    cmul_pm(w[4], w[1], w[5], w[3]);
-    cmul_pm(w[8], w[1], w[9], w[7]);
-    cmul_pm(w[12], w[1], w[13], w[11]);
-    cmul_pm(w[16], w[1], w[17], w[15]);
-    cmul_pm(w[20], w[1], w[21], w[19]);
-    cmul_pm(w[24], w[1], w[25], w[23]);
-    cmul_pm(w[28], w[1], w[29], w[27]);
-    cmul_pm(w[8], w[2], w[10], w[6]);
-    cmul_pm(w[16], w[2], w[18], w[14]);
-    cmul_pm(w[24], w[2], w[26], w[22]);
-    w[30] = cmul(w[28], w[2]);
-    w[31] = cmul(w[28], w[3]);
-  } else {
-    static_assert(r == 2, "twiddle mode 1 for radix 2, 4, 8, 16, 32");
-  }
-}
-
 // The r - 1 twiddles W^{j k}, j = 1 .. r-1, of one butterfly.
 //   TWM = 0: every one read from the pass table (row j - 1).
 //   TWM = 1: the rows tw_loaded<r> names read, the others derived
