@@ -224,9 +224,21 @@ fft_status_t launch_stockham(const KernelEntry *k, int dir, const float2 *in, fl
   int64_t grid = (rows + k->TB - 1) / k->TB;
   if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;
   if (grid > 0x7fffffffLL) return FFT_ERR_INVALID_SIZE;
+  // Programmatic stream serialization: the kernel waits (griddepcontrol.wait)
+  // for the previous kernel of the stream before any global access, so it
+  // may be launched while that kernel's last CTAs are still running.
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(k->threads);
+  cfg.dynamicSmemBytes = k->smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr.val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
   void *args[] = {&a};
-  FFTGB_CUDA(cudaLaunchKernel(k->fn[dir > 0 ? 1 : 0], dim3((unsigned)grid), dim3(k->threads),
-                              args, k->smem, st));
+  FFTGB_CUDA(cudaLaunchKernelExC(&cfg, k->fn[dir > 0 ? 1 : 0], args));
   return FFT_OK;
 }
 

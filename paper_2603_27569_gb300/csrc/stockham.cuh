@@ -387,6 +387,13 @@ stockham_kernel(StockhamArgs args) {
   static_assert(P % SC::max_radix() == 0, "every radix must divide P");
   constexpr int T = N / P;
   extern __shared__ __align__(128) float2 smem[];
+  // Launched with programmatic stream serialization: this grid's CTAs may
+  // become resident while the previous kernel of the stream is finishing;
+  // nothing global is touched before that kernel has completed and its
+  // writes are visible.  Then the next kernel's CTAs may launch as this
+  // grid's CTAs retire.  (Without the launch attribute both are no-ops.)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int b = threadIdx.x / T;
   const int lt = threadIdx.x - b * T;
   float2 *buf = smem + b * N;
