@@ -49,6 +49,10 @@ column_kernel(ColumnArgs args) {
   constexpr int T = L / P;
   constexpr int NT = C * T;
   extern __shared__ __align__(128) float2 smem[];
+  // Programmatic dependent launch (see stockham_kernel): phase 2 may become
+  // resident while phase 1 finishes, but reads nothing before it completed.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int c = threadIdx.x % C;
   const int lt = threadIdx.x / C;
   const int tiles_per_mat = args.ncols / C;

@@ -57,6 +57,10 @@ __global__ void __launch_bounds__(TB *(N / P), (65536 / (TB * (N / P) * 128)) > 
 filter_kernel(FilterArgs a) {
   constexpr int T = N / P;
   extern __shared__ __align__(128) float2 smem[];
+  // Programmatic dependent launch (see stockham_kernel): nothing global
+  // before the previous kernel of the stream has completed.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int b = threadIdx.x / T;
   const int lt = threadIdx.x - b * T;
   float2 *buf = smem + b * N;
@@ -257,7 +261,7 @@ static fft_status_t filter_launch(const FilterKernel &k, FilterArgs &a, cudaStre
   const int64_t grid = (a.batch + k.tb - 1) / k.tb;
   if (grid > 0x7fffffffLL) return FFT_ERR_INVALID_SIZE;
   void *args[] = {&a};
-  return cuda_status(cudaLaunchKernel(k.fn, dim3((unsigned)grid), dim3(k.threads), args, k.smem, st));
+  return cuda_status(launch_pdl(k.fn, dim3((unsigned)grid), dim3(k.threads), k.smem, st, args));
 }
 
 fft_status_t fft_filter_forward(fft_plan_t plan, const void *x, const void *H, void *y,

@@ -76,6 +76,11 @@ struct fft_plan_impl {
 
 // Helpers implemented in api.cu, shared with the other units.
 fft_status_t cuda_status(cudaError_t e);
+// Launch with programmatic stream serialization: the kernel must begin with
+// griddepcontrol.wait (no global access before the previous kernel of the
+// stream has completed), and may then let the next one launch early.
+cudaError_t launch_pdl(const void *fn, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       void **args);
 fft_status_t build_twiddles(fft_plan_impl *pl, const std::vector<TwSeg> &segs);
 std::vector<TwSeg> pass_segments(const KernelEntry &k, int64_t &offset);
 const KernelEntry *find_stockham(int N, int P, int TB, const int *radix, int npass, int twm);
