@@ -313,8 +313,9 @@ static fft_status_t launch_column(const KernelEntry *k, int dir, const ColumnArg
   if (grid > 0x7fffffffLL) return FFT_ERR_INVALID_SIZE;
   ColumnArgs a = ca;
   void *args[] = {&a};
-  // Programmatic dependent launch up to 2048-point columns; the 4096-point
-  // column kernels (one CTA of 128 KiB per SM) measured 1-2.6 % slower with it.
+  // Programmatic dependent launch up to 2048-point columns (the kernels that
+  // carry the griddepcontrol instructions); the 4096-point column kernels (one
+  // CTA of 128 KiB per SM) measured 1-4 % slower with it.
   if (k->N <= 2048) {
     FFTGB_CUDA(launch_pdl(k->fn[dir > 0 ? 1 : 0], dim3((unsigned)grid), dim3(k->threads),
                           k->smem, st, args));

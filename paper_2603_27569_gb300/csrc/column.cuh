@@ -49,10 +49,14 @@ column_kernel(ColumnArgs args) {
   constexpr int T = L / P;
   constexpr int NT = C * T;
   extern __shared__ __align__(128) float2 smem[];
-  // Programmatic dependent launch (see stockham_kernel): phase 2 may become
-  // resident while phase 1 finishes, but reads nothing before it completed.
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  // Programmatic dependent launch (see stockham_kernel) up to 2048-point
+  // columns: phase 2 may become resident while phase 1 finishes, but reads
+  // nothing before it completed.  The 4096-point kernels (one 128 KiB CTA
+  // per SM, many waves) are launched plainly and carry neither instruction.
+  if constexpr (L <= 2048) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  }
   const int c = threadIdx.x % C;
   const int lt = threadIdx.x / C;
   const int tiles_per_mat = args.ncols / C;
