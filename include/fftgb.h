@@ -194,6 +194,10 @@ fft_status_t fft_plan_config(fft_plan_t *out, int N, int64_t batch, int directio
  * aligned; in == out is allowed, partial overlap is FFT_ERR_INVALID_VALUE.
  * For a ragged plan, in and out are the packed base pointers the plan's
  * offsets index.  stream: cudaStream_t or NULL.  Asynchronous.
+ * Stream order holds as for any launch: the single-CTA, filter and
+ * (up to 2048-point) column kernels use programmatic dependent launch, so
+ * their CTAs may become resident while the previous kernel of the stream
+ * finishes, but they read and write nothing before it has completed.
  */
 fft_status_t fft_exec(fft_plan_t plan, const void *in, void *out, void *stream);
 
