@@ -289,3 +289,28 @@ def test_beyond_one_cta(N, direction):
         y, info = run(x[:2], direction, config=cfg)
         assert info["n1"] == cfg["n1"] and info["cluster_split"] == cfg["cluster_split"]
         check(x[:2], y, direction)
+
+
+@pytest.mark.parametrize("N,batch", [(4096, 3000), (16384, 1000)])
+def test_dependent_calls_back_to_back(N, batch):
+    # Kernels launched with programmatic dependent launch may become resident
+    # while the previous kernel of the stream runs; each call here reads the
+    # previous call's output with no host synchronisation in between (forward,
+    # inverse, forward, inverse, in place on the second buffer), so a kernel
+    # that touched memory before the previous one completed would be caught.
+    x = synth.gaussian((batch, N), seed=21)
+    a = to_dev(x)
+    b = torch.empty_like(a)
+    fwd, inv = fg.Plan(N, batch, fg.FFT_FORWARD), fg.Plan(N, batch, fg.FFT_INVERSE)
+    fwd(a, out=b)
+    inv(b, out=b)
+    fwd(b, out=a)
+    inv(a, out=b)
+    X = to_host(a)
+    y = to_host(b)
+    torch.cuda.synchronize()
+    fwd.close()
+    inv.close()
+    rows = np.array([0, 1, batch // 2, batch - 1])
+    check(x[rows], X[rows], fg.FFT_FORWARD, tol=4 * TOL_FP32)
+    assert rel_l2_rows(y, x).max() <= 4 * TOL_FP32
