@@ -8,9 +8,12 @@ than the 129 MB L2, so no flush is needed between timed calls.
 
 Metric: GFLOPS = sum of 5 N log2 N per transform / time (paper Sec. VI-A),
 and the fraction of HBM bandwidth at 16 N bytes per transform.  The value
-times K steps of back-to-back calls (CUDA events at the ends only); the
-per-size times and the roofline kernel's launch time come from a second
-pass of K steps with an event pair around every call.
+times K steps of back-to-back calls (CUDA events at the ends only).  The
+per-size times and the roofline kernel's launch time come from a third pass
+that runs K back-to-back calls of each (N, direction) plan with events at
+their ends; a second pass with an event pair around every call gives the
+isolated per-call times beside them.  SM clocks, power and throttle reasons
+are sampled through NVML every few milliseconds across all three passes.
 
 Printed: ONE JSON line (rank 0).  Extra objects report the per-size numbers,
 the forward+backward spectral filter against plain transforms, and the
@@ -86,32 +89,94 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+    """SM clock, power and clock-event (throttle) reasons of this GPU, sampled
+    every few milliseconds through NVML (libnvidia-ml, read-only queries) on
+    a background thread while the timed region runs; nvidia-smi (100 ms
+    period) if NVML cannot be loaded."""
 
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
     Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
-        self.idx = gpu_index
-        self.lines = []
-        self.proc = None
+    def __init__(self, cuda_index: int, period_s: float = 0.002):
+        self.cuda_index = cuda_index
+        self.period = period_s
+        self.rows = []           # (time, sm_mhz, max_mhz, power_w, [reason names])
+        self.source = None
         self.t_on = self.t_off = None
+        self._stop = threading.Event()
+        self._th = None
+        self._proc = None
+
+    def _nvml_handle(self):
+        import ctypes
+
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        try:  # the CUDA device's UUID identifies it whatever CUDA_VISIBLE_DEVICES says
+            import torch
+
+            uuid = str(torch.cuda.get_device_properties(self.cuda_index).uuid)
+            uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+            if lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(h)) != 0:
+                raise OSError("uuid lookup failed")
+        except Exception:
+            if lib.nvmlDeviceGetHandleByIndex_v2(self.cuda_index, ctypes.byref(h)) != 0:
+                raise OSError("no NVML handle")
+        reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        return lib, h, reasons
+
+    def _nvml_loop(self, lib, h, reasons_fn):
+        import ctypes
+
+        clk, mx, pw = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_uint()
+        rs = ctypes.c_ulonglong()
+        lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))  # NVML_CLOCK_SM
+        while not self._stop.is_set():
+            t = time.time()
+            if lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0:
+                p = pw.value / 1000.0 if lib.nvmlDeviceGetPowerUsage(h, ctypes.byref(pw)) == 0 \
+                    else None
+                r = rs.value if reasons_fn(h, ctypes.byref(rs)) == 0 else 0
+                names = [n for bit, n in self.REASONS.items() if r & bit]
+                self.rows.append((t, float(clk.value), float(mx.value), p, names))
+            self._stop.wait(self.period)
+
+    def _smi_loop(self):
+        for line in self._proc.stdout:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                names = [n for n, v in zip(["hw_slowdown", "hw_thermal_slowdown",
+                                            "sw_thermal_slowdown", "sw_power_cap"], f[6:10])
+                         if v.lower() == "active"]
+                self.rows.append((time.time(), float(f[2]), float(f[3]), None, names))
+            except ValueError:
+                continue
 
     def start(self):
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-i", str(self.idx), "-lms", "100"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.th = threading.Thread(target=self._read, daemon=True)
-            self.th.start()
-        except (OSError, ValueError):
-            self.proc = None
-
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append((time.time(), line.strip()))
+            lib, h, reasons_fn = self._nvml_handle()
+            self.source = f"NVML every {self.period * 1e3:.0f} ms"
+            self._th = threading.Thread(target=self._nvml_loop, args=(lib, h, reasons_fn),
+                                        daemon=True)
+        except (OSError, AttributeError):
+            try:
+                self._proc = subprocess.Popen(
+                    ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                     "-i", str(self.cuda_index), "-lms", "100"],
+                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                self.source = "nvidia-smi every 100 ms"
+                self._th = threading.Thread(target=self._smi_loop, daemon=True)
+            except (OSError, ValueError):
+                return
+        self._th.start()
 
     def mark_on(self):
         self.t_on = time.time()
@@ -120,31 +185,30 @@ class ClockSampler:
         self.t_off = time.time()
 
     def stop(self):
-        if self.proc:
-            self.proc.terminate()
+        self._stop.set()
+        if self._proc:
+            self._proc.terminate()
             try:
-                self.proc.wait(timeout=5)
+                self._proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
-                self.proc.kill()
+                self._proc.kill()
+        if self._th:
+            self._th.join(timeout=5)
 
     def summary(self):
-        if not self.lines:
+        if not self.rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        rows = []
-        for t, ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 10:
-                continue
-            try:
-                rows.append((t, float(f[2]), float(f[3]), f[6:10]))
-            except ValueError:
-                continue
+        rows = list(self.rows)
         win = [r for r in rows if self.t_on and self.t_on <= r[0] <= (self.t_off or r[0])]
         use = win if win else rows[-3:]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in use for i, v in enumerate(r[3]) if v.lower() == "active"})
-        return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": max(r[2] for r in use),
-                "reasons": reasons, "samples": len(use), "in_window": bool(win)}
+        reasons = sorted({n for r in use for n in r[4]})
+        pw = [r[3] for r in use if r[3] is not None]
+        return {"sm_mhz": statistics.median(r[1] for r in use),
+                "sm_mhz_min": min(r[1] for r in use),
+                "sm_max_mhz": max(r[2] for r in use), "reasons": reasons,
+                "samples": len(use), "in_window": bool(win),
+                "power_w_median": round(statistics.median(pw), 1) if pw else None,
+                "source": self.source}
 
 
 def traffic_for(kernel_key: str):
@@ -289,7 +353,7 @@ def run_ours(args):
 
     clocks = ClockSampler(local)
     clocks.start()
-    time.sleep(1.0)  # let the sampler emit before the timed region
+    time.sleep(0.2)  # let the sampler start before the timed region
     evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
             for _ in keys] for _ in range(args.steps)]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -312,6 +376,16 @@ def run_ours(args):
     for s in range(args.steps):
         step(evs[s])
     c_end.record(stream)
+    # Back-to-back pass per (N, direction): K calls of one plan in a row,
+    # events at their ends only; the average call time of a plan as it runs
+    # in a stream of such calls (the roofline kernel's launch time).
+    b2b_ev = [[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+              for _ in keys]
+    for i, k in enumerate(keys):
+        b2b_ev[i][0].record(stream)
+        for s in range(args.steps):
+            plans[k].exec(x, out=y, stream=stream)
+        b2b_ev[i][1].record(stream)
     torch.cuda.synchronize()
     clocks.mark_off()
     if world > 1:
@@ -327,31 +401,39 @@ def run_ours(args):
     peak, peak_kind = peaks()
     per_key_ms = {k: statistics.mean(evs[s][i][0].elapsed_time(evs[s][i][1])
                                      for s in range(args.steps)) for i, k in enumerate(keys)}
+    b2b_ms = {k: shard.max_over_ranks(b2b_ev[i][0].elapsed_time(b2b_ev[i][1])) / args.steps
+              for i, k in enumerate(keys)}
+
     def pct(i, q):
         v = sorted(evs[s][i][0].elapsed_time(evs[s][i][1]) for s in range(args.steps))
         return v[min(len(v) - 1, int(q * (len(v) - 1) + 0.5))]
 
+    def frac(ms):
+        return round(16.0 * POINTS / (ms * 1e-3) / 1e9 / peak, 4)
+
     per_size = {}
     for N in SIZES:
-        f_ms, i_ms = per_key_ms[(N, fg.FFT_FORWARD)], per_key_ms[(N, fg.FFT_INVERSE)]
-        fi, ii = keys.index((N, fg.FFT_FORWARD)), keys.index((N, fg.FFT_INVERSE))
-        gbs_f = 16.0 * POINTS / (f_ms * 1e-3) / 1e9
-        gbs_i = 16.0 * POINTS / (i_ms * 1e-3) / 1e9
-        info = plans[(N, fg.FFT_FORWARD)].info()
+        kf, ki = (N, fg.FFT_FORWARD), (N, fg.FFT_INVERSE)
+        fi, ii = keys.index(kf), keys.index(ki)
+        info = plans[kf].info()
         per_size[str(N)] = {
-            "fwd_us": round(f_ms * 1e3, 2), "inv_us": round(i_ms * 1e3, 2),
-            "fwd_gflops": round(flops(N, POINTS // N) / (f_ms * 1e-3) / 1e9, 1),
-            "inv_gflops": round(flops(N, POINTS // N) / (i_ms * 1e-3) / 1e9, 1),
-            "fwd_frac_hbm": round(gbs_f / peak, 4), "inv_frac_hbm": round(gbs_i / peak, 4),
-            "fwd_us_p10_p50_p90": [round(pct(fi, q) * 1e3, 2) for q in (0.1, 0.5, 0.9)],
-            "inv_us_p10_p50_p90": [round(pct(ii, q) * 1e3, 2) for q in (0.1, 0.5, 0.9)],
+            "fwd_us": round(b2b_ms[kf] * 1e3, 2), "inv_us": round(b2b_ms[ki] * 1e3, 2),
+            "fwd_frac_hbm": frac(b2b_ms[kf]), "inv_frac_hbm": frac(b2b_ms[ki]),
+            "fwd_gflops": round(flops(N, POINTS // N) / (b2b_ms[kf] * 1e-3) / 1e9, 1),
+            "inv_gflops": round(flops(N, POINTS // N) / (b2b_ms[ki] * 1e-3) / 1e9, 1),
+            "fwd_us_isolated": round(per_key_ms[kf] * 1e3, 2),
+            "inv_us_isolated": round(per_key_ms[ki] * 1e3, 2),
+            "fwd_frac_hbm_isolated": frac(per_key_ms[kf]),
+            "inv_frac_hbm_isolated": frac(per_key_ms[ki]),
+            "fwd_us_isolated_p10_p50_p90": [round(pct(fi, q) * 1e3, 2) for q in (0.1, 0.5, 0.9)],
+            "inv_us_isolated_p10_p50_p90": [round(pct(ii, q) * 1e3, 2) for q in (0.1, 0.5, 0.9)],
             "path": {1: "single_cta", 2: "fourstep"}.get(info["path"], info["path"]),
             "radix": info["radix"], "points_per_thread": info["points_per_thread"],
             "twiddle_mode": info["twiddle_mode"], "grid_ctas": info["grid_ctas"],
             "tma_slabs": info["tma_slabs"], "n1": info["n1"],
         }
-    dom = max(keys, key=lambda k: per_key_ms[k])
-    dom_ms = per_key_ms[dom]
+    dom = max(keys, key=lambda k: b2b_ms[k])
+    dom_ms = b2b_ms[dom]
     dom_info = plans[dom].info()
     kind = ("staged" if dom_info["tma_slabs"] else "stockham") if dom_info["path"] == 1 \
         else "fourstep"
@@ -361,7 +443,11 @@ def run_ours(args):
                 "frac": round(achieved / peak, 4), "traffic": traffic_for(kname),
                 "kernel": kname, "peak_source": f"{peak_kind} hbm_gbs",
                 "algorithmic_bytes_per_launch": 16 * POINTS,
-                "launch_us": round(dom_ms * 1e3, 2)}
+                "launch_us": round(dom_ms * 1e3, 2),
+                "launch_us_timing": "average over K back-to-back calls of this plan, events at "
+                                    "the ends (CUDA events on the launching stream)",
+                "launch_us_isolated": round(per_key_ms[dom] * 1e3, 2),
+                "frac_isolated": frac(per_key_ms[dom])}
     total_fft_bytes = 16.0 * POINTS * len(keys)
     overall_frac = total_fft_bytes / (ms_per_step * 1e-3) / 1e9 / peak
     gpu_launches = sum(launches_per_exec[k] for k in keys) * args.steps
@@ -420,8 +506,10 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "points_per_call": POINTS, "sizes": SIZES,
                        "calls_per_step": len(keys), "l2": "inputs larger than L2 (256 MiB > 129 MB)",
                        "timing": "value: K steps of back-to-back calls, CUDA events at the ends only; "
-                                 "per_size and roofline: a second pass of K steps with an event pair "
-                                 "around every call",
+                                 "per_size *_isolated: a second pass of K steps with an event pair "
+                                 "around every call; per_size fwd_us/inv_us and the roofline launch "
+                                 "time: a third pass, K back-to-back calls of each plan, events at "
+                                 "the ends",
                        "ms_per_step_per_call_pass": round(ms_per_step_per_call_pass, 4),
                        "parallelism": f"weak, {world} GPU(s), independent batches per rank"},
             "frac_hbm_step": round(overall_frac, 4),

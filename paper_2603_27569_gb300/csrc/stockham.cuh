@@ -375,10 +375,25 @@ __device__ __forceinline__ void prefetch_l2_warp(const void *p, long long bytes,
   }
 }
 
+// Row loads of pass 0: thread lt of row `row` takes the points lt + m T.
+template <int N, int P>
+__device__ __forceinline__ void load_row(float2 (&a)[P], const float2 *src, int lt) {
+  constexpr int T = N / P;
+#pragma unroll
+  for (int m = 0; m < P; ++m) a[m] = __ldcs(src + lt + m * T);
+}
+
 // Persistent over tiles of TB rows: CTA c handles tiles c, c + G, c + 2G, ...
 // (G = gridDim.x; a grid of one CTA per tile runs the loop once).  Warp 0
 // asks the bulk-copy engine to prefetch the CTA's NEXT tile into L2, so HBM
 // streams the next rows while this tile computes.
+//
+// Epilogue: the output held in register m (or register pair 2j, 2j + 1) is
+// stored, and the register is at once refilled with the next tile's input
+// point m.  The next tile's loads (from L2, prefetched) are then in flight
+// while this tile's stores drain, instead of being issued after them: the
+// SM's read and write paths to L2 work at the same time.  The buffer is
+// rewritten only after the end-of-tile barrier, so nothing else changes.
 template <int N, int P, int TB, int D, class SC, int TWM>
 __global__ void __launch_bounds__(TB *(N / P))
 stockham_kernel(StockhamArgs args) {
@@ -398,7 +413,17 @@ stockham_kernel(StockhamArgs args) {
   const int lt = threadIdx.x - b * T;
   float2 *buf = smem + b * N;
   const long long ntiles = (args.batch + TB - 1) / TB;
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  long long tile = blockIdx.x;
+  float2 a[P];
+  // Rows past the batch exist only in the last tile (all later tiles of
+  // this CTA would be past it too), so an inactive row ends the loop.
+  if (tile < ntiles && tile * TB + b < args.batch) {
+    load_row<N, P>(a, args.in + (tile * TB + b) * N, lt);
+  } else {
+#pragma unroll
+    for (int m = 0; m < P; ++m) a[m] = make_float2(0.f, 0.f);
+  }
+  for (; tile < ntiles; tile += gridDim.x) {
     const long long next = tile + gridDim.x;
     auto prefetch_next = [&]() {
       if (next < ntiles && threadIdx.x < 32) {
@@ -415,15 +440,8 @@ stockham_kernel(StockhamArgs args) {
     if (SC::npass == 1 || !first) prefetch_next();
     const long long row = tile * TB + b;
     const bool active = row < args.batch;
-    float2 a[P];
-    const float2 *src = args.in + row * N;
-    if (active) {
-#pragma unroll
-      for (int m = 0; m < P; ++m) a[m] = __ldcs(src + lt + m * T);
-    } else {
-#pragma unroll
-      for (int m = 0; m < P; ++m) a[m] = make_float2(0.f, 0.f);
-    }
+    const long long nrow = next * TB + b;
+    const bool load_next = next < ntiles && nrow < args.batch;
     // Opaque per tile: keeps the compiler from hoisting the loop-invariant
     // twiddle reads and exchange addresses out of the tile loop into
     // (occupancy-costly) registers.
@@ -439,6 +457,7 @@ stockham_kernel(StockhamArgs args) {
         NoTw{});
     if (active) {
       float2 *dst = args.out + row * N;
+      const float2 *nsrc = args.in + (load_next ? nrow : row) * N;
       const float s = args.scale;
       if constexpr (PAIR_LAST) {
 #pragma unroll
@@ -446,10 +465,17 @@ stockham_kernel(StockhamArgs args) {
           const float2 u = cscale(a[2 * j], s), v = cscale(a[2 * j + 1], s);
           __stcs(reinterpret_cast<float4 *>(dst + final_index_pair<N, P, SC>(ltp, j)),
                  make_float4(u.x, u.y, v.x, v.y));
+          if (load_next) {
+            a[2 * j] = __ldcs(nsrc + lt + (2 * j) * T);
+            a[2 * j + 1] = __ldcs(nsrc + lt + (2 * j + 1) * T);
+          }
         }
       } else {
 #pragma unroll
-        for (int m = 0; m < P; ++m) __stcs(dst + final_index<N, P, SC>(ltp, m), cscale(a[m], s));
+        for (int m = 0; m < P; ++m) {
+          __stcs(dst + final_index<N, P, SC>(ltp, m), cscale(a[m], s));
+          if (load_next) a[m] = __ldcs(nsrc + lt + m * T);
+        }
       }
     }
     if (next < ntiles) __syncthreads();  // the next tile rewrites the buffer
