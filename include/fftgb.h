@@ -138,7 +138,9 @@ typedef struct {
                                a scratch copy of the whole batch               */
 } fft_config_t;
 
-/* Human-readable name of a status code (static string, never NULL). */
+/* Human-readable name of a status code (static string, never NULL).
+ * Paper: Sec. II-A (the problem statement whose calls these codes report on;
+ * the paper defines no error reporting). */
 const char *fft_status_string(fft_status_t status);
 
 /*
@@ -154,15 +156,20 @@ const char *fft_status_string(fft_status_t status);
  * (generated in FP64 on the GPU, rounded to FP32) and synchronises once.
  * On success *out holds a plan to free with fft_destroy(); on failure *out is
  * set to NULL.
- * Paper: Sec. IV-D (synthesis rules) decides the factorisation; the
- * radix schedule follows Sec. V-B/V-D.
+ * Paper: Sec. II-A (the batched transform, fft_plan(N, batch, direction));
+ * Sec. IV-D (synthesis rules) decides the factorisation; the radix schedule
+ * follows Sec. V-B/V-D.
  */
 fft_status_t fft_plan(fft_plan_t *out, int N, int64_t batch, int direction);
 
 /* As fft_plan with a precision (fft_precision_t) and FFT_FLAG_* flags
  * (N > 16384: FP32 only, FFT_FLAG_FORCE_SINGLE_CTA is FFT_ERR_NOT_SUPPORTED).
  * The tensor-core precisions support N in {256, 4096, 16384} only
- * (FFT_ERR_NOT_SUPPORTED otherwise). */
+ * (FFT_ERR_NOT_SUPPORTED otherwise).
+ * Paper: Sec. II-A (the transform); Sec. V-C, Eqs. 5-6 (the DFT block as a
+ * real matrix product: FFT_PREC_FP16X2 / BF16X2); Sec. IX-A (mixed precision
+ * for radar data: the 16-bit storage precisions); Sec. IV-B, Eq. 3
+ * (FFT_FLAG_FORCE_FOURSTEP). */
 fft_status_t fft_plan_ex(fft_plan_t *out, int N, int64_t batch, int direction,
                          int precision, int flags);
 
@@ -174,6 +181,9 @@ fft_status_t fft_plan_ex(fft_plan_t *out, int N, int64_t batch, int direction,
  * split.
  * Writes min(count, capacity) entries to out (out may be NULL) and returns
  * the total count (0 for an unsupported N).
+ * Paper: Sec. IV-C (radix selection) and Sec. V-D (the per-size kernel
+ * configurations, Table of multi-size kernels) -- the space the autotuner
+ * searches.
  */
 int fft_list_configs(int N, fft_config_t *out, int capacity);
 
@@ -182,6 +192,7 @@ int fft_list_configs(int N, fft_config_t *out, int capacity);
  * fft_list_configs (used by the autotuner and by tests that cover every
  * configuration).  flags as in fft_plan_ex, except the FORCE_* flags.
  * FFT_ERR_NOT_SUPPORTED if the configuration is not compiled in.
+ * Paper: Sec. V-D (one explicit kernel configuration per size).
  */
 fft_status_t fft_plan_config(fft_plan_t *out, int N, int64_t batch, int direction,
                              int flags, const fft_config_t *config);
@@ -198,6 +209,8 @@ fft_status_t fft_plan_config(fft_plan_t *out, int N, int64_t batch, int directio
  * (up to 2048-point) column kernels use programmatic dependent launch, so
  * their CTAs may become resident while the previous kernel of the stream
  * finishes, but they read and write nothing before it has completed.
+ * Paper: Sec. II-A (fft_exec(plan, in, out, stream) over the DFT defined
+ * there); Sec. II-B (Stockham autosort: natural-order output).
  */
 fft_status_t fft_exec(fft_plan_t plan, const void *in, void *out, void *stream);
 
@@ -207,20 +220,27 @@ fft_status_t fft_exec(fft_plan_t plan, const void *in, void *out, void *stream);
  * pipelining the copies with the transforms in chunks.  Blocks until the
  * result is in host_out.  Page-locked (pinned) host memory gives full copy
  * bandwidth; pageable memory works but is slower.  Not for ragged plans.
+ * Paper: Sec. II-A (the same transform; the host copies stand in for the
+ * unified memory of Sec. III-A, which a discrete GPU does not have).
  */
 fft_status_t fft_exec_host(fft_plan_t plan, const void *host_in, void *host_out,
                            void *stream);
 
-/* Free a plan and all device memory it owns.  NULL is accepted. */
+/* Free a plan and all device memory it owns.  NULL is accepted.
+ * Paper: Sec. II-A (the plan of the problem statement). */
 fft_status_t fft_destroy(fft_plan_t plan);
 
-/* Describe what a plan chose (path, radix schedule, threads, split). */
+/* Describe what a plan chose (path, radix schedule, threads, split).
+ * Paper: Sec. IV-D (synthesis rules) and Sec. V-D (kernel configurations):
+ * what the planner chose for the problem of Sec. II-A. */
 fft_status_t fft_plan_info(fft_plan_t plan, fft_plan_info_t *info);
 
 /*
  * Read and clear the plan's device status word.  Synchronises the device.
  * Returns FFT_OK, or the first error a kernel recorded (FFT_ERR_TIMEOUT for a
  * bounded wait that ran out).
+ * Paper: Sec. II-A (reports on the execution of the problem statement's
+ * transform; the paper defines no device error reporting).
  */
 fft_status_t fft_last_device_status(fft_plan_t plan);
 
@@ -230,16 +250,20 @@ fft_status_t fft_last_device_status(fft_plan_t plan);
  * if host_out is non-NULL, min(*count, capacity) entries are copied.
  * Each entry is W_M^e = exp(-2 pi i e / M) for the (M, e) that
  * fft_twiddle_index() reports for the same position.
+ * Paper: Sec. V-A and V-B (the twiddle factors W of each pass; here
+ * precomputed in FP64 and rounded to FP32 instead of sincos chains).
  */
 fft_status_t fft_twiddle_table(fft_plan_t plan, void *host_out, int64_t capacity,
                                int64_t *count);
-/* Position -> (M, e) of the twiddle table entry. */
+/* Position -> (M, e) of the twiddle table entry.
+ * Paper: Sec. V-A and V-B (as fft_twiddle_table). */
 fft_status_t fft_twiddle_index(fft_plan_t plan, int64_t pos, int64_t *M, int64_t *e);
 
 /*
  * fft_ragged_plan — a batch of `count` transforms of mixed lengths and
- * directions, executed in ONE persistent launch (longest transforms first,
- * work claimed through a device counter).
+ * directions, executed by persistent launches that claim work longest
+ * first through device counters (two kernels: rows of 16384 and 8192, then
+ * units of rows of <= 4096 points).
  * N[i]: power of two in [16, 16384] (2..8 give FFT_ERR_NOT_SUPPORTED);
  * direction[i]: -1 or +1;
  * in_offset[i], out_offset[i]: start of transform i, in complex elements,
@@ -250,7 +274,7 @@ fft_status_t fft_twiddle_index(fft_plan_t plan, int64_t pos, int64_t *M, int64_t
  * 16384 by whole CTAs, rows of 8192 by CTA halves, rows of <= 4096 in
  * 4096-point units by CTA quarters.  fft_exec replays a CUDA graph (counter
  * reset + kernel) captured for the (in, out) pair; a new pair re-captures.
- * Reference: the batched radar FFTs of Sec. II-D with mixed lengths.
+ * Paper: Sec. II-D (batched radar FFTs; here with mixed lengths).
  */
 fft_status_t fft_ragged_plan(fft_plan_t *out, int count, const int *N,
                              const int *direction, const int64_t *in_offset,
@@ -263,13 +287,17 @@ fft_status_t fft_ragged_plan(fft_plan_t *out, int count, const int *N,
  * store the fastest in the process-wide cache used by later plans.  If
  * cache_path is non-NULL the whole cache is also written there as JSON
  * (keyed by GPU name, N, direction, precision).  Allocates its own buffers.
+ * Paper: Sec. IV-C (radix selection) and Sec. V-D (the kernel-selection
+ * table per size), chosen here by measurement on the current GPU.
  */
 fft_status_t fft_autotune(int N, int direction, int precision, int64_t batch,
                           const char *cache_path);
 /* Load a JSON cache written by fft_autotune (entries for other GPUs are
- * ignored).  A missing file is FFT_ERR_INVALID_VALUE. */
+ * ignored).  A missing file is FFT_ERR_INVALID_VALUE.
+ * Paper: Sec. V-D (as fft_autotune). */
 fft_status_t fft_autotune_load(const char *cache_path);
-/* Forget every autotuned choice (plans fall back to the built-in table). */
+/* Forget every autotuned choice (plans fall back to the built-in table).
+ * Paper: Sec. V-D (as fft_autotune). */
 fft_status_t fft_autotune_clear(void);
 
 /*
@@ -285,6 +313,8 @@ fft_status_t fft_autotune_clear(void);
  *   bytes.
  * All pointers are device pointers, 16-byte aligned (8 for grad_h); all
  * calls are asynchronous on stream.
+ * Paper: Sec. II-D (range compression as a matched filter in the frequency
+ * domain) and Sec. IX-A (the fused FFT / matched-filter pipeline).
  */
 fft_status_t fft_filter_apply(const void *X, const void *H, void *Z, int N,
                               int64_t batch, int conj_h, float scale, void *stream);
@@ -317,6 +347,8 @@ fft_status_t fft_filter_grad_h(const void *X, const void *G, void *grad_H, int N
  *   then grad_x in place; so grad_x may not overlap g_y or X_saved
  *   (FFT_ERR_INVALID_VALUE).
  * Device pointers, 16-byte aligned; asynchronous on stream.
+ * Paper: Sec. IX-A (FFT fused with matched filtering in one kernel) and
+ * Sec. II-D (SAR range compression).
  */
 fft_status_t fft_filter_plan(fft_plan_t *out, int N, int64_t batch);
 fft_status_t fft_filter_forward(fft_plan_t plan, const void *x, const void *H, void *y,
@@ -344,15 +376,17 @@ fft_status_t fft_filter_backward(fft_plan_t plan, const void *g_y, const void *H
  * allowed, any other overlap of the two extents is FFT_ERR_INVALID_VALUE;
  * fft_exec_host is FFT_ERR_NOT_SUPPORTED.  Each CTA reads its columns whole
  * before writing them, so the in-place transform is safe.
+ * Paper: Sec. II-D (azimuth compression as batched 1-D FFTs over the other
+ * matrix dimension) and Sec. IX-A (the corner turn).
  */
 fft_status_t fft_plan_columns(fft_plan_t *out, int L, int64_t ncols, int64_t nmat,
                               int64_t row_stride, int64_t mat_stride, int direction,
                               int flags);
 
 /*
- * fft_fourstep_noalloc — the two-phase four-step transform (same kernels and
- * results as a plan made with FFT_FLAG_FORCE_FOURSTEP) for callers that must
- * not allocate device memory.  The paper has no counterpart: this entry
+ * fft_fourstep_noalloc — the two-phase four-step transform (same kernels,
+ * tables and results, bit for bit, as a plan made with
+ * FFT_FLAG_FORCE_FOURSTEP) for callers that must not allocate device memory.  The paper has no counterpart: this entry
  * point exists for users of the library whose code may not call cudaMalloc
  * while it runs, e.g. a real-time pipeline whose memory is fixed at start-up
  * or code that hands the device heap to its own allocator.  It takes no plan
@@ -367,7 +401,8 @@ fft_status_t fft_plan_columns(fft_plan_t *out, int L, int64_t ncols, int64_t nma
  * FFT_INVERSE (inverse scaled by 1/N).  Asynchronous on `stream`.
  * The first call on a device sets that device up (resolves the arrays'
  * addresses, fills the tables, synchronises the device): make it before any
- * stream capture.  All calls share the one scratch array, which keeps the
+ * stream capture.  The set-up belongs to the device's context: after
+ * cudaDeviceReset the next call sets the device up again (same rule).  All calls share the one scratch array, which keeps the
  * last call's contents; calls whose work overlaps on the GPU race with each
  * other, so serialise them (e.g. one stream).
  */

@@ -306,8 +306,8 @@ static fft_status_t launch_split(const KernelEntry *k, int dir, const float2 *in
   return FFT_OK;
 }
 
-static fft_status_t launch_column(const KernelEntry *k, int dir, const ColumnArgs &ca,
-                                  cudaStream_t st) {
+fft_status_t launch_column(const KernelEntry *k, int dir, const ColumnArgs &ca,
+                           cudaStream_t st) {
   const int64_t grid = ca.nmat * (ca.ncols / k->TB);
   if (grid <= 0) return FFT_OK;
   if (grid > 0x7fffffffLL) return FFT_ERR_INVALID_SIZE;

@@ -14,10 +14,13 @@
 // until the process exits (16 MiB of scratch + 512 KiB of tables).  The
 // first call on a device sets that device up (resolves the arrays'
 // addresses, fills the twiddle tables, synchronises the device); make that
-// first call outside any stream capture.  Every call shares the one scratch
-// array, so calls whose work overlaps on the GPU (for instance on two
-// streams) race; the intermediate is fully rewritten by phase 1 before
-// phase 2 reads it, so nothing needs clearing between calls.
+// first call outside any stream capture.  The set-up is tied to the device's
+// current context: after cudaDeviceReset (which reloads the module and so
+// zeroes both arrays) the next call sets the device up again.  Every call
+// shares the one scratch array, so calls whose work overlaps on the GPU (for
+// instance on two streams) race; the intermediate is fully rewritten by
+// phase 1 before phase 2 reads it, so nothing needs clearing between calls.
+#include <cuda.h>  // CUcontext / CUresult for two driver entry points (not linked)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -52,8 +55,9 @@ struct SizeSetup {
 
 struct DeviceSetup {
   bool ready = false;
-  float2 *scratch = nullptr;  // device address of g_scratch on this device
-  float2 *tw = nullptr;       // device address of g_tw on this device
+  unsigned long long ctx_id = 0;  // context the tables were filled in (0: unknown)
+  float2 *scratch = nullptr;      // device address of g_scratch on this device
+  float2 *tw = nullptr;           // device address of g_tw on this device
   SizeSetup size[kSizes];
 };
 
@@ -75,70 +79,129 @@ bool split(int N, int *n1, int *n2) {
   return true;
 }
 
-// Per-pass tables of column kernel k written from `off` on; returns the end.
-int64_t fill_pass_tables(const KernelEntry *k, float2 *tw, int64_t off) {
+// Entries of the per-pass tables of column kernel k.
+int64_t pass_table_entries(const KernelEntry *k) {
+  int64_t n = 0;
   int p = k->radix[0];
   for (int s = 1; s < k->npass; ++s) {
-    const int r = k->radix[s];
+    n += (int64_t)(k->radix[s] - 1) * p;
+    p *= k->radix[s];
+  }
+  return n;
+}
+
+// One generator launch; its status is checked here (cudaLaunchKernel returns
+// it directly), not read back from the thread's shared last-error slot.
+cudaError_t launch_gen(const void *fn, int64_t n, void **args) {
+  return cudaLaunchKernel(fn, dim3((unsigned)((n + 255) / 256)), dim3(256), args, 0, nullptr);
+}
+
+// Per-pass tables of column kernel k written from `off` on; returns the end.
+cudaError_t fill_pass_tables(const KernelEntry *k, float2 *tw, int64_t &off) {
+  int p = k->radix[0];
+  for (int s = 1; s < k->npass; ++s) {
+    int r = k->radix[s];
     const int64_t n = (int64_t)(r - 1) * p;
-    gen_pass_twiddles<<<(unsigned)((n + 255) / 256), 256>>>(tw + off, p, r);
+    float2 *dst = tw + off;
+    void *args[] = {&dst, &p, &r};
+    const cudaError_t e = launch_gen((const void *)&gen_pass_twiddles, n, args);
+    if (e != cudaSuccess) return e;
     off += n;
     p *= r;
   }
-  return off;
+  return cudaSuccess;
+}
+
+// Process-unique id of the calling thread's current context (cuCtxGetId),
+// through driver entry points the runtime hands out; false if unavailable.
+bool current_context_id(unsigned long long *id) {
+  typedef CUresult (*GetCurrent)(CUcontext *);
+  typedef CUresult (*GetId)(CUcontext, unsigned long long *);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void *f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = (GetCurrent)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (GetId)f;
+  });
+  CUcontext ctx = nullptr;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+  return get_id(ctx, id) == CUDA_SUCCESS;
 }
 
 fft_status_t setup_device(int dev, DeviceSetup **out) {
   std::lock_guard<std::mutex> lk(g_mu);
   DeviceSetup &d = g_dev[dev];
-  if (!d.ready) {
-    // Host code may not take the arrays' addresses directly: resolve the
-    // device addresses with the runtime, for the current device.
-    if (cudaGetSymbolAddress((void **)&d.scratch, g_scratch) != cudaSuccess ||
-        cudaGetSymbolAddress((void **)&d.tw, g_tw) != cudaSuccess) {
-      cudaGetLastError();
-      return FFT_ERR_CUDA;
-    }
-    int64_t off = 0;
-    for (int e = kMinLog2; e <= kMaxLog2; ++e) {
-      SizeSetup &z = d.size[e - kMinLog2];
-      const int N = 1 << e;
-      if (!split(N, &z.n1, &z.n2)) return FFT_ERR_NOT_SUPPORTED;
-      z.k1 = default_column(z.n2, 1);
-      z.k2 = default_column(z.n1, 0);
-      z.tw1 = off;
-      off = fill_pass_tables(z.k1, d.tw, off);
-      z.tw2 = off;
-      off = fill_pass_tables(z.k2, d.tw, off);
-      // phase-1 twiddle grids W_N^{c lt} [lt][c] and W_N^{c T m} [m][c]
-      const int T1 = z.n2 / z.k1->P;
-      const int64_t na = (int64_t)T1 * z.n1, nb = (int64_t)z.k1->P * z.n1;
-      if (off + na + nb > kTwEntries) return FFT_ERR_NOT_SUPPORTED;
-      z.twa = off;
-      gen_grid_twiddles<<<(unsigned)((na + 255) / 256), 256>>>(d.tw + off, z.n1, 1, N, na);
-      off += na;
-      z.twb = off;
-      gen_grid_twiddles<<<(unsigned)((nb + 255) / 256), 256>>>(d.tw + off, z.n1, T1, N, nb);
-      off += nb;
-    }
-    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
-      return FFT_ERR_CUDA;
-    d.ready = true;
+  // Host code may not take the arrays' addresses directly: resolve the
+  // device addresses with the runtime, for the current device (this also
+  // makes the device's context current).  A failure is returned as
+  // FFT_ERR_CUDA; the runtime's last-error slot keeps it, as for any failed
+  // runtime call, and nothing of the caller's is cleared.
+  float2 *scratch = nullptr, *tw = nullptr;
+  if (cudaGetSymbolAddress((void **)&scratch, g_scratch) != cudaSuccess ||
+      cudaGetSymbolAddress((void **)&tw, g_tw) != cudaSuccess)
+    return FFT_ERR_CUDA;
+  unsigned long long ctx = 0;
+  const bool have_ctx = current_context_id(&ctx);
+  if (d.ready && d.scratch == scratch && d.tw == tw && (!have_ctx || d.ctx_id == ctx)) {
+    *out = &d;
+    return FFT_OK;
   }
+  d.ready = false;
+  d.scratch = scratch;
+  d.tw = tw;
+  // Lay out every size's tables first and check the total against the
+  // array before anything is written.
+  int64_t off = 0;
+  for (int e = kMinLog2; e <= kMaxLog2; ++e) {
+    SizeSetup &z = d.size[e - kMinLog2];
+    const int N = 1 << e;
+    if (!split(N, &z.n1, &z.n2)) return FFT_ERR_NOT_SUPPORTED;
+    z.k1 = default_column(z.n2, 1);
+    z.k2 = default_column(z.n1, 0);
+    const int T1 = z.n2 / z.k1->P;
+    z.tw1 = off;
+    off += pass_table_entries(z.k1);
+    z.tw2 = off;
+    off += pass_table_entries(z.k2);
+    z.twa = off;  // phase-1 twiddle grid W_N^{c lt}, [lt][c]
+    off += (int64_t)T1 * z.n1;
+    z.twb = off;  // phase-1 twiddle grid W_N^{c T m}, [m][c]
+    off += (int64_t)z.k1->P * z.n1;
+  }
+  if (off > kTwEntries) return FFT_ERR_NOT_SUPPORTED;
+  for (int e = kMinLog2; e <= kMaxLog2; ++e) {
+    SizeSetup &z = d.size[e - kMinLog2];
+    if (ensure_smem_attr(z.k1) != FFT_OK || ensure_smem_attr(z.k2) != FFT_OK)
+      return FFT_ERR_CUDA;
+    int64_t o = z.tw1;
+    if (fill_pass_tables(z.k1, tw, o) != cudaSuccess) return FFT_ERR_CUDA;
+    o = z.tw2;
+    if (fill_pass_tables(z.k2, tw, o) != cudaSuccess) return FFT_ERR_CUDA;
+    int64_t cols = z.n1, step = 1, M = 1 << e;
+    int64_t na = (int64_t)(z.n2 / z.k1->P) * z.n1, nb = (int64_t)z.k1->P * z.n1;
+    float2 *dst = tw + z.twa;
+    void *aa[] = {&dst, &cols, &step, &M, &na};
+    if (launch_gen((const void *)&gen_grid_twiddles, na, aa) != cudaSuccess) return FFT_ERR_CUDA;
+    float2 *dstb = tw + z.twb;
+    int64_t stepb = z.n2 / z.k1->P;
+    void *ab[] = {&dstb, &cols, &stepb, &M, &nb};
+    if (launch_gen((const void *)&gen_grid_twiddles, nb, ab) != cudaSuccess) return FFT_ERR_CUDA;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) return FFT_ERR_CUDA;
+  d.ctx_id = have_ctx ? ctx : 0;
+  d.ready = true;
   *out = &d;
   return FFT_OK;
-}
-
-fft_status_t launch(const KernelEntry *k, int dir, const ColumnArgs &ca, cudaStream_t st) {
-  const int64_t grid = ca.nmat * (ca.ncols / k->TB);
-  if (grid <= 0) return FFT_OK;
-  if (grid > 0x7fffffffLL) return FFT_ERR_INVALID_SIZE;
-  ColumnArgs a = ca;
-  void *args[] = {&a};
-  return cudaLaunchKernel(k->fn[dir > 0 ? 1 : 0], dim3((unsigned)grid), dim3(k->threads), args,
-                          k->smem, st) == cudaSuccess
-             ? FFT_OK
-             : FFT_ERR_CUDA;
 }
 
 }  // namespace
@@ -180,7 +243,7 @@ extern "C" fft_status_t fft_fourstep_noalloc(const void *in, void *out, int N, i
   c1.ncols = z.n1;
   c1.ntot = N;
   c1.scale = 1.f;
-  s = launch(z.k1, direction, c1, st);
+  s = launch_column(z.k1, direction, c1, st);
   if (s != FFT_OK) return s;
   ColumnArgs c2{};
   c2.in = d->scratch;
@@ -194,5 +257,5 @@ extern "C" fft_status_t fft_fourstep_noalloc(const void *in, void *out, int N, i
   c2.ncols = z.n2;
   c2.ntot = N;
   c2.scale = direction == FFT_INVERSE ? 1.0f / (float)N : 1.0f;
-  return launch(z.k2, direction, c2, st);
+  return launch_column(z.k2, direction, c2, st);
 }

@@ -81,6 +81,10 @@ fft_status_t cuda_status(cudaError_t e);
 // stream has completed), and may then let the next one launch early.
 cudaError_t launch_pdl(const void *fn, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                        void **args);
+// One column-kernel launch (column.cuh) with the library's launch policy:
+// programmatic dependent launch for columns up to 2048 points.
+struct ColumnArgs;
+fft_status_t launch_column(const KernelEntry *k, int dir, const ColumnArgs &ca, cudaStream_t st);
 fft_status_t build_twiddles(fft_plan_impl *pl, const std::vector<TwSeg> &segs);
 std::vector<TwSeg> pass_segments(const KernelEntry &k, int64_t &offset);
 const KernelEntry *find_stockham(int N, int P, int TB, const int *radix, int npass, int twm);

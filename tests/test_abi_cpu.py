@@ -161,3 +161,25 @@ def test_column_plan_validates_on_host(L):
     assert L.fft_plan_columns(ctypes.byref(h), 256, 16, 2, 16, 1000, -1, 0) == INVALID_VALUE
     assert L.fft_plan_columns(ctypes.byref(h), 256, 16, 1, 16, 4096, 0, 0) == INVALID_VALUE
     assert L.fft_plan_columns(ctypes.byref(h), 256, 16, 1, 16, 4096, -1, 0x4) == INVALID_VALUE
+
+
+def test_every_declaration_cites_its_passage():
+    """Each exported function's comment (the nearest comment block before its
+    declaration) names the paper passage it implements, or says the paper has
+    no counterpart."""
+    text = open(HEADER).read()
+    body = text[text.index("#ifdef __cplusplus"):]
+    missing = []
+    for m in re.finditer(r"\b(fft_[a-z0-9_]+)\s*\(", body):
+        before = body[:m.start()]
+        if before.rstrip().endswith("*/") is False and "/*" not in before:
+            missing.append(m.group(1))
+            continue
+        comment = before[before.rindex("/*"):]
+        if "*/" not in comment:        # the name appears inside a comment
+            continue
+        comment = comment[:comment.index("*/")]
+        if not re.search(r"Paper: (Sec\.|Eq\.|Table)", comment) and \
+                "paper has no counterpart" not in comment.lower():
+            missing.append(m.group(1))
+    assert not missing, f"declarations without a cited passage: {sorted(set(missing))}"

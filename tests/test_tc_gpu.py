@@ -1,8 +1,9 @@
 """Split-precision tensor-core FFT against the FP64 oracle.
 
-Target: relative L2 error <= 1e-5 per transform for FP16 hi+lo.  BF16 hi+lo
-keeps ~16 significant bits, so its error is reported as measured (and bounded
-here at 1e-4).  The per-size error table is printed (pytest -s)."""
+Target: relative L2 error <= 1e-5 per transform for FP16 hi+lo and for BF16
+hi+lo alike (BF16 hi+lo keeps ~16 significant bits of each operand, enough
+for the measured <= 6e-6 at these sizes).  The per-size error table is
+printed (pytest -s)."""
 import numpy as np
 import pytest
 
@@ -15,7 +16,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 PREC = {"fp16x2": fg.FFT_PREC_FP16X2, "bf16x2": fg.FFT_PREC_BF16X2}
-BOUND = {"fp16x2": TOL_SPLIT, "bf16x2": 1e-4}
+BOUND = {"fp16x2": TOL_SPLIT, "bf16x2": TOL_SPLIT}
 
 
 @pytest.fixture(scope="module", autouse=True)
