@@ -525,7 +525,8 @@ def run_ours(args):
 
 def bench_ragged(fg, synth, torch, dev):
     """20000 mixed transforms (log2 N ~ U{8..14}, mixed directions, seed 0) in
-    one persistent launch (CUDA graph) vs one plain launch per (N, direction)
+    one persistent launch (CUDA graph), with the autotuned routine per class
+    (and with the built-in routines), vs one plain launch per (N, direction)
     group over the same transforms gathered contiguously (gathering untimed)."""
     import numpy as np
 
@@ -533,21 +534,32 @@ def bench_ragged(fg, synth, torch, dev):
     total = d["total"]
     x = torch.from_numpy(synth.gaussian(total, seed=0)).to(dev)
     y = torch.empty_like(x)
-    plan = fg.fft_ragged_plan(d["N"], d["direction"], d["offset"], d["offset"])
     st = torch.cuda.current_stream(dev)
     flop = sum(5.0 * int(n) * math.log2(int(n)) for n in d["N"])
-    for _ in range(3):
-        fg.fft_exec(plan, x, y, st)
-    torch.cuda.synchronize()
     reps = 10
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(st)
-    for _ in range(reps):
-        fg.fft_exec(plan, x, y, st)
-    b.record(st)
-    torch.cuda.synchronize()
-    rag_ms = a.elapsed_time(b) / reps
-    fg.fft_destroy(plan)
+
+    def time_plan(flags):
+        plan = fg.fft_ragged_plan(d["N"], d["direction"], d["offset"], d["offset"], flags)
+        for _ in range(3):
+            fg.fft_exec(plan, x, y, st)
+        torch.cuda.synchronize()
+        a.record(st)
+        for _ in range(reps):
+            fg.fft_exec(plan, x, y, st)
+        b.record(st)
+        torch.cuda.synchronize()
+        classes = {f"{int(N)}{'f' if dirn < 0 else 'i'}": fg.fft_ragged_class_config(plan, int(N), dirn)
+                   for N in np.unique(d["N"]) for dirn in (-1, 1)
+                   if np.any((d["N"] == N) & (d["direction"] == dirn))}
+        info = fg.fft_plan_info(plan)
+        fg.fft_destroy(plan)
+        return a.elapsed_time(b) / reps, classes, info
+
+    builtin_ms, _, _ = time_plan(fg.FFT_FLAG_NO_AUTOTUNE_CACHE)
+    # the autotuner times each class's routines on its rows (untimed here)
+    rag_ms, classes, info = time_plan(fg.FFT_FLAG_RAGGED_AUTOTUNE)
+    fg.fft_autotune_clear()
     # plain baseline: one plan per (N, direction) over contiguous groups
     groups = []
     for N in np.unique(d["N"]):
@@ -576,10 +588,19 @@ def bench_ragged(fg, synth, torch, dev):
     return {"workload": "20000 transforms, log2 N ~ U{8..14}, mixed fwd/inv, N(0,1) seed 0, "
                         "packed in draw order",
             "bytes": 16 * total, "ragged_ms": round(rag_ms, 4), "plain_ms": round(plain_ms, 4),
+            "ragged_builtin_routines_ms": round(builtin_ms, 4),
+            "ragged_launches": 1, "ragged_grid_ctas": info["grid_ctas"],
+            "ragged_threads_per_cta": info["threads_per_cta"],
             "plain_launches": len(groups),
             "ragged_gflops": round(flop / (rag_ms * 1e-3) / 1e9, 1),
             "plain_gflops": round(flop / (plain_ms * 1e-3) / 1e9, 1),
-            "ragged_vs_plain": round(plain_ms / rag_ms, 3)}
+            "ragged_frac_hbm": round(16 * total / (rag_ms * 1e-3) / 1e9 / peaks()[0], 4),
+            "ragged_vs_plain": round(plain_ms / rag_ms, 3),
+            "autotuned_routines": {k: {"P": c["points_per_thread"], "radix": c["radix"],
+                                       "twiddle_mode": c["twiddle_mode"],
+                                       "rows_per_unit": c["transforms_per_cta"],
+                                       "threads_per_row": 512 // c["transforms_per_cta"]}
+                                   for k, c in classes.items()}}
 
 
 def bench_tc(fg, synth, torch, dev):

@@ -79,11 +79,16 @@ typedef enum {
  * adjoint(inverse G = F^H / N) = F / N.  The backward pass of a layer that
  * applies F (or G) applies this plan to the incoming gradient. */
 #define FFT_FLAG_ADJOINT 0x10
+/* fft_ragged_plan only: time every compiled routine of each class (N,
+ * direction) of the batch on that class's rows and use the fastest; the
+ * choices are kept in a process-wide cache that later ragged plans use
+ * (unless they pass FFT_FLAG_NO_AUTOTUNE_CACHE). */
+#define FFT_FLAG_RAGGED_AUTOTUNE 0x20
 
 /* Execution paths reported by fft_plan_info(). */
 #define FFT_PATH_SINGLE_CTA 1  /* Stockham, every pass inside one CTA        */
 #define FFT_PATH_FOURSTEP 2    /* column FFTs + twiddle, then row FFTs        */
-#define FFT_PATH_RAGGED 3      /* persistent ragged launch                    */
+#define FFT_PATH_RAGGED 3      /* ragged batch: one persistent launch         */
 #define FFT_PATH_TENSORCORE 4  /* split-precision tensor-core radix-16 DFT    */
 #define FFT_PATH_FILTER 5      /* fused spectral filter (fft_filter_plan)     */
 #define FFT_PATH_COLUMNS 6     /* strided column transforms (fft_plan_columns) */
@@ -261,24 +266,48 @@ fft_status_t fft_twiddle_index(fft_plan_t plan, int64_t pos, int64_t *M, int64_t
 
 /*
  * fft_ragged_plan — a batch of `count` transforms of mixed lengths and
- * directions, executed by persistent launches that claim work longest
- * first through device counters (two kernels: rows of 16384 and 8192, then
- * units of rows of <= 4096 points).
+ * directions, executed in ONE persistent launch: one 512-thread CTA per SM
+ * claims work units longest N first through a device counter; a unit fills
+ * the CTA (512 P / N rows of one (N, direction), N / P threads each, P = 16
+ * or 32 points per thread).
  * N[i]: power of two in [16, 16384] (2..8 give FFT_ERR_NOT_SUPPORTED);
  * direction[i]: -1 or +1;
  * in_offset[i], out_offset[i]: start of transform i, in complex elements,
  * inside the packed buffers passed to fft_exec(); every offset must be a
  * multiple of 2 (16-byte alignment).  Host arrays are copied; the caller keeps
- * ownership.  flags: FFT_FLAG_UNNORMALIZED_INVERSE (FFT_FLAG_NO_AUTOTUNE_CACHE
- * is accepted and has no effect).  Work is claimed longest-first: rows of
- * 16384 by whole CTAs, rows of 8192 by CTA halves, rows of <= 4096 in
- * 4096-point units by CTA quarters.  fft_exec replays a CUDA graph (counter
- * reset + kernel) captured for the (in, out) pair; a new pair re-captures.
+ * ownership.  flags: FFT_FLAG_UNNORMALIZED_INVERSE; FFT_FLAG_RAGGED_AUTOTUNE
+ * (time the compiled routines of each class on its rows now and use the
+ * fastest, remembered for later ragged plans); FFT_FLAG_NO_AUTOTUNE_CACHE
+ * (ignore remembered choices: built-in routines).  fft_ragged_class_config
+ * reports each class's routine.  fft_exec replays a CUDA graph (counter
+ * reset + the one kernel) captured for the (in, out) pair; a new pair
+ * re-captures.
  * Paper: Sec. II-D (batched radar FFTs; here with mixed lengths).
  */
 fft_status_t fft_ragged_plan(fft_plan_t *out, int count, const int *N,
                              const int *direction, const int64_t *in_offset,
                              const int64_t *out_offset, int flags);
+
+/* The routine a ragged plan runs for its class (N, direction): points per
+ * thread, radix schedule, twiddle mode, rows per unit (transforms_per_cta),
+ * threads_per_cta (512) and path FFT_PATH_RAGGED.  FFT_ERR_INVALID_VALUE if
+ * the plan is not ragged or holds no transform of that class.
+ * Paper: Sec. IV-C (radix selection) and Sec. V-D (per-size kernel
+ * configuration), per class of the Sec. II-D batch. */
+fft_status_t fft_ragged_class_config(fft_plan_t plan, int N, int direction,
+                                     fft_config_t *config);
+
+/* The routines compiled for class N of a ragged batch (path
+ * FFT_PATH_RAGGED), as fft_list_configs does for plain plans; returns the
+ * total count and writes min(count, capacity) entries to out (may be NULL).
+ * Paper: Sec. IV-C (radix selection) and Sec. V-D (per-size kernel
+ * configurations). */
+int fft_ragged_list_configs(int N, fft_config_t *out, int capacity);
+/* Make `config` (one of fft_ragged_list_configs(N)) the remembered routine
+ * for class (N, direction) of later ragged plans, as the autotuner would;
+ * fft_autotune_clear forgets it.  FFT_ERR_NOT_SUPPORTED if not compiled in.
+ * Paper: Sec. V-D (one explicit kernel configuration per size). */
+fft_status_t fft_ragged_choose(int N, int direction, const fft_config_t *config);
 
 /*
  * fft_autotune — time the candidate configurations (points per thread, radix
@@ -296,7 +325,8 @@ fft_status_t fft_autotune(int N, int direction, int precision, int64_t batch,
  * ignored).  A missing file is FFT_ERR_INVALID_VALUE.
  * Paper: Sec. V-D (as fft_autotune). */
 fft_status_t fft_autotune_load(const char *cache_path);
-/* Forget every autotuned choice (plans fall back to the built-in table).
+/* Forget every autotuned choice, plain and ragged (plans fall back to the
+ * built-in table).
  * Paper: Sec. V-D (as fft_autotune). */
 fft_status_t fft_autotune_clear(void);
 

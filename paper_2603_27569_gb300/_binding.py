@@ -25,6 +25,8 @@ __all__ = [
     "fft_filter_forward", "fft_filter_backward", "FFT_PATH_FILTER",
     "PlanInfo", "Config", "EXPORTED_SYMBOLS", "fft_list_configs", "fft_plan_config",
     "fft_fourstep_noalloc", "FFT_NOALLOC_MAX_POINTS", "fft_plan_columns", "FFT_PATH_COLUMNS",
+    "fft_ragged_class_config", "FFT_FLAG_RAGGED_AUTOTUNE", "fft_ragged_list_configs",
+    "fft_ragged_choose",
 ]
 
 FFT_FORWARD = -1
@@ -36,6 +38,7 @@ FFT_FLAG_FORCE_SINGLE_CTA = 0x2
 FFT_FLAG_FORCE_FOURSTEP = 0x4
 FFT_FLAG_NO_AUTOTUNE_CACHE = 0x8
 FFT_FLAG_ADJOINT = 0x10
+FFT_FLAG_RAGGED_AUTOTUNE = 0x20
 FFT_PATH_SINGLE_CTA, FFT_PATH_FOURSTEP, FFT_PATH_RAGGED, FFT_PATH_TENSORCORE = 1, 2, 3, 4
 FFT_PATH_FILTER = 5
 FFT_PATH_COLUMNS = 6
@@ -117,6 +120,9 @@ _SIGS = {
     "fft_twiddle_table": ([_vp, _vp, _i64, ctypes.POINTER(_i64)], _i32),
     "fft_twiddle_index": ([_vp, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_i64)], _i32),
     "fft_ragged_plan": ([ctypes.POINTER(_vp), _i32, _vp, _vp, _vp, _vp, _i32], _i32),
+    "fft_ragged_class_config": ([_vp, _i32, _i32, ctypes.POINTER(Config)], _i32),
+    "fft_ragged_list_configs": ([_i32, _vp, _i32], _i32),
+    "fft_ragged_choose": ([_i32, _i32, ctypes.POINTER(Config)], _i32),
     "fft_autotune": ([_i32, _i32, _i32, _i64, ctypes.c_char_p], _i32),
     "fft_autotune_load": ([ctypes.c_char_p], _i32),
     "fft_autotune_clear": ([], _i32),
@@ -254,6 +260,26 @@ def fft_ragged_plan(N, direction, in_offset, out_offset, flags: int = 0) -> int:
     _check(lib().fft_ragged_plan(ctypes.byref(h), len(N), N.ctypes.data, d.ctypes.data,
                                  oi.ctypes.data, oo.ctypes.data, flags), "fft_ragged_plan")
     return h.value
+
+
+def fft_ragged_class_config(plan: int, N: int, direction: int) -> dict:
+    """The routine a ragged plan runs for its class (N, direction)."""
+    c = Config()
+    _check(lib().fft_ragged_class_config(plan, N, direction, ctypes.byref(c)),
+           "fft_ragged_class_config")
+    return c.as_dict()
+
+
+def fft_ragged_list_configs(N: int) -> list:
+    n = lib().fft_ragged_list_configs(N, None, 0)
+    arr = (Config * max(n, 1))()
+    lib().fft_ragged_list_configs(N, ctypes.cast(arr, _vp), n)
+    return [arr[i].as_dict() for i in range(n)]
+
+
+def fft_ragged_choose(N: int, direction: int, config: dict) -> None:
+    c = Config.from_dict(config)
+    _check(lib().fft_ragged_choose(N, direction, ctypes.byref(c)), "fft_ragged_choose")
 
 
 def fft_autotune(N: int, direction: int, precision: int = 0, batch: int = 0,

@@ -1079,6 +1079,7 @@ fft_status_t fft_plan_info(fft_plan_t plan, fft_plan_info_t *info) {
   info->cluster_split = pl->path == FFT_PATH_SINGLE_CTA ? pl->k_single->split : 0;
   info->l2_chunk_rows = pl->l2_rows;
   if (pl->k_l2) info->grid_ctas = (int)pl->l2_grid;
+  if (pl->path == FFT_PATH_RAGGED) info->threads_per_cta = 512;  // one persistent launch
   return FFT_OK;
 }
 

@@ -244,9 +244,12 @@ fft_status_t fft_autotune_load(const char *cache_path) {
 }
 
 fft_status_t fft_autotune_clear(void) {
-  std::lock_guard<std::mutex> lk(g_mu);
-  g_cache.clear();
-  g_env_loaded = true;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_cache.clear();
+    g_env_loaded = true;
+  }
+  ragged_clear_choices();
   return FFT_OK;
 }
 

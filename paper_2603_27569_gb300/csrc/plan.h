@@ -127,6 +127,7 @@ void filter_destroy(fft_plan_impl *pl);
 // Ragged path (ragged.cu)
 fft_status_t ragged_exec(fft_plan_impl *pl, const float2 *in, float2 *out, cudaStream_t st);
 void ragged_destroy(fft_plan_impl *pl);
+void ragged_clear_choices();  // forget the ragged autotuner's choices
 
 }  // namespace fftgb
 

@@ -322,24 +322,30 @@ __device__ __forceinline__ void pass_apply(float2 (&a)[P], const PT &t) {
   }
 }
 
-// run_passes for one row per thread group with the whole CTA as barrier
-// domain and the swizzled row layout, reading each pass's twiddle rows
-// ahead of its exchange barrier (PassTw).  hk() as in run_passes.
-template <int N, int P, int D, class SC, int S, int TWM, bool PAIR_LAST, class HK, class PT>
+// A warp-wide barrier: for thread groups that lie inside one warp.
+struct WarpBarrier {
+  __device__ __forceinline__ void sync() const { __syncwarp(); }
+};
+
+// run_passes for one row per thread group with the swizzled row layout,
+// reading each pass's twiddle rows ahead of its exchange barrier (PassTw).
+// hk() as in run_passes; br: the group's barrier (the whole CTA by default).
+template <int N, int P, int D, class SC, int S, int TWM, bool PAIR_LAST, class HK, class PT,
+          class BR = CtaBarrier>
 __device__ __forceinline__ void run_passes_early(float2 (&a)[P], int lt, float2 *buf,
                                                  const float2 *__restrict__ tw, const HK &hk,
-                                                 const PT &pre) {
+                                                 const PT &pre, const BR &br = BR{}) {
   pass_apply<N, P, D, SC, S, TWM>(a, pre);
   if constexpr (S + 1 < SC::npass) {
     constexpr bool PN = PAIR_LAST && S + 2 == SC::npass;
-    if constexpr (S > 0) __syncthreads();  // every read of the buffer is done
+    if constexpr (S > 0) br.sync();  // every read of the buffer is done
     pass_write<N, P, SC, S>(a, lt, buf, SwizzledRow{});
     PassTw<N, P, SC, S + 1, TWM, PN> next;
     next.load(lt, tw);
-    __syncthreads();
+    br.sync();
     if constexpr (S == 0) hk();
     pass_read<N, P, SC, S, SwizzledRow, PN>(a, lt, buf, SwizzledRow{});
-    run_passes_early<N, P, D, SC, S + 1, TWM, PAIR_LAST>(a, lt, buf, tw, hk, next);
+    run_passes_early<N, P, D, SC, S + 1, TWM, PAIR_LAST>(a, lt, buf, tw, hk, next, br);
   }
 }
 

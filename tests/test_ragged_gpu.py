@@ -145,3 +145,81 @@ def test_ragged_argument_errors():
                               np.zeros(0, np.int64), np.zeros(0, np.int64))
     fg.fft_exec(plan, 16, 16)                                     # empty: nothing to do
     fg.fft_destroy(plan)
+
+
+def _explicit_case(sizes_dirs_counts, seed):
+    """Rows of given (N, direction, count), packed in an interleaved order."""
+    N, D = [], []
+    for n, dirn, cnt in sizes_dirs_counts:
+        N += [n] * cnt
+        D += [dirn] * cnt
+    perm = np.random.Generator(np.random.PCG64(seed)).permutation(len(N))
+    N = np.array(N, np.int32)[perm]
+    D = np.array(D, np.int32)[perm]
+    off = np.concatenate([[0], np.cumsum(N.astype(np.int64))[:-1]]).astype(np.int64)
+    d = {"N": N, "direction": D, "offset": off, "total": int(N.sum())}
+    return d, synth.gaussian(d["total"], seed=seed + 100)
+
+
+@pytest.mark.parametrize("N", [16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 8192, 16384])
+def test_every_compiled_routine_matches_oracle(N):
+    """Each compiled routine of class N, forced through fft_ragged_choose, on
+    one and a half units of rows per direction (a partial last unit), mixed
+    with rows of another class."""
+    other = 1024 if N != 1024 else 256
+    try:
+        for cfg in fg.fft_ragged_list_configs(N):
+            fg.fft_ragged_choose(N, fg.FFT_FORWARD, cfg)
+            fg.fft_ragged_choose(N, fg.FFT_INVERSE, cfg)
+            per = cfg["transforms_per_cta"]
+            cnt = per + max(1, per // 2)
+            d, x = _explicit_case([(N, -1, cnt), (N, 1, cnt), (other, 1, 3)], seed=N)
+            plan = fg.fft_ragged_plan(d["N"], d["direction"], d["offset"], d["offset"])
+            assert fg.fft_ragged_class_config(plan, N, fg.FFT_FORWARD) == cfg
+            assert fg.fft_ragged_class_config(plan, N, fg.FFT_INVERSE) == cfg
+            fg.fft_destroy(plan)
+            y, _ = run_ragged(d, x)
+            check_rows(d, x, y, range(len(d["N"])))
+    finally:
+        fg.fft_autotune_clear()
+
+
+def test_one_launch_plan_info_and_class_configs():
+    d, x = packed_case(300, seed=9, lo=8, hi=14)
+    plan = fg.fft_ragged_plan(d["N"], d["direction"], d["offset"], d["offset"],
+                              fg.FFT_FLAG_NO_AUTOTUNE_CACHE)
+    info = fg.fft_plan_info(plan)
+    assert info["path"] == fg.FFT_PATH_RAGGED and info["threads_per_cta"] == 512
+    for N in np.unique(d["N"]):
+        for dirn in (-1, 1):
+            present = np.any((d["N"] == N) & (d["direction"] == dirn))
+            if present:
+                c = fg.fft_ragged_class_config(plan, int(N), dirn)
+                assert c == fg.fft_ragged_list_configs(int(N))[0]      # the built-in routine
+                # a unit fills its worker: the whole CTA for 16384, a 256-thread half otherwise
+                assert c["threads_per_cta"] == (512 if N == 16384 else 256)
+                assert c["transforms_per_cta"] * int(N) == c["threads_per_cta"] * c["points_per_thread"]
+            else:
+                with pytest.raises(fg.FFTError):
+                    fg.fft_ragged_class_config(plan, int(N), dirn)
+    fg.fft_destroy(plan)
+
+
+def test_autotune_flag_chooses_and_remembers_per_class():
+    d, x = packed_case(600, seed=11, lo=8, hi=14)
+    try:
+        y, _ = run_ragged(d, x, flags=fg.FFT_FLAG_RAGGED_AUTOTUNE)
+        check_rows(d, x, y, range(0, 600, 7))
+        tuned = fg.fft_ragged_plan(d["N"], d["direction"], d["offset"], d["offset"],
+                                   fg.FFT_FLAG_RAGGED_AUTOTUNE)
+        later = fg.fft_ragged_plan(d["N"], d["direction"], d["offset"], d["offset"])
+        for N in np.unique(d["N"]):
+            for dirn in (-1, 1):
+                if np.any((d["N"] == N) & (d["direction"] == dirn)):
+                    c = fg.fft_ragged_class_config(tuned, int(N), dirn)
+                    assert c in fg.fft_ragged_list_configs(int(N))
+                    assert fg.fft_ragged_class_config(later, int(N), dirn) == c
+        fg.fft_destroy(tuned)
+        fg.fft_destroy(later)
+    finally:
+        fg.fft_autotune_clear()
