@@ -71,6 +71,35 @@ def test_every_compiled_config_matches_oracle(N, direction):
         check(x, y, direction)
 
 
+@pytest.mark.parametrize("N", [256, 512, 1024, 2048, 4096, 8192, 16384])
+@pytest.mark.parametrize("direction", [fg.FFT_FORWARD, fg.FFT_INVERSE])
+def test_persistent_configs_over_several_rounds_of_tiles(N, direction):
+    """Every persistent single-CTA configuration with each CTA taking at least
+    two tiles and a partial last tile: the epilogue that loads a CTA's next
+    tile while it stores the current one runs on every round but the last.
+    Rows of the second round and of the tail are checked against the oracle,
+    every row for being finite."""
+    cfgs = [c for c in fg.fft_list_configs(N)
+            if c["path"] == fg.FFT_PATH_SINGLE_CTA and c["ctas_per_sm"] == -1
+            and not c["tma_slabs"] and not c["cluster_split"]]
+    assert cfgs
+    for cfg in cfgs:
+        tb = cfg["transforms_per_cta"]
+        probe = fg.Plan(N, 1, direction, config=cfg)
+        G = probe.info()["grid_ctas"]
+        probe.close()
+        assert G > 0
+        batch = 2 * G * tb + tb + max(1, tb // 2)   # two full rounds, a third partial round
+        x = synth.gaussian((batch, N), seed=11 * N + cfg["points_per_thread"] + tb)
+        y, info = run(x, direction, config=cfg)
+        assert info["grid_ctas"] == G and np.isfinite(y).all()
+        rng = np.random.Generator(np.random.PCG64(N + tb))
+        second = np.arange(G * tb, G * tb + min(4 * tb, 64))        # round two, first CTAs
+        tail = np.arange(max(0, batch - 2 * tb - 3), batch)        # last tiles, partial tile
+        rows = np.unique(np.concatenate([second, tail, rng.integers(G * tb, batch, 24)]))
+        check(x[rows], y[rows], direction)
+
+
 @pytest.mark.parametrize("N", [512, 1024, 2048, 4096, 8192, 16384, 32768])
 def test_full_size_sampled_rows(N):
     # the benchmark's size: 2^25 points (256 MiB) per call, batch = 2^25 / N
