@@ -1,5 +1,5 @@
-// Fused spectral filter: y = IFFT(FFT(x) * H) in one kernel per row (two
-// from N = 8192 on, see variant()), and its backward, for the SAR range-compression layer (paper Sec. II-D; the fused
+// Fused spectral filter: y = IFFT(FFT(x) * H) in one kernel per row, and its
+// backward, for the SAR range-compression layer (paper Sec. II-D; the fused
 // FFT -> matched filter -> IFFT pipeline is the paper's future work, Sec. IX-A).
 //
 // After any forward Stockham transform (stockham.cuh) thread lt holds output
@@ -10,17 +10,16 @@
 //
 //   forward   y = G (F x * H)              (conj_h: * conj(H))       FM_FWD
 //             X_save = F x                 (optional, for the backward)
-//             (N >= 8192: FM_SPEC into X_save or y, then FM_MULINV)
+//             (N >= 8192: filter_fwd2_kernel, the two halves as calls)
 //   backward  g_z = G^H g_y = F g_y / N                              FM_SPEC
 //             grad_H = sum_rows conj(X) * g_z   (fft_filter_grad_h: 32-row
 //                      chunks, then a fixed-order pairwise tree)
 //             grad_x = F^H (conj(H) * g_z)                           FM_MULINV
-// The backward keeps g_z in grad_x's buffer: FM_SPEC writes it there, the
-// reduction reads it, and FM_MULINV transforms it in place (a CTA reads its
-// whole row before it writes it).  Keeping grad_H's per-frequency sums in
-// registers inside one backward kernel instead needs P more complex
-// registers per thread; on GB300 that forced 16 points per thread with
-// spills, and the three-step backward measured faster at every N.
+//             (N >= 8192: filter_bwd2_kernel, one kernel whose grad_H
+//              partial sums live in tensor memory, then the same tree)
+// Below 8192 the backward keeps g_z in grad_x's buffer: FM_SPEC writes it
+// there, the reduction reads it, and FM_MULINV transforms it in place (a CTA
+// reads its whole row before it writes it).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -126,6 +125,241 @@ filter_kernel(FilterArgs a) {
   }
 }
 
+// One-kernel forward for 32 points per thread (N >= 8192): the row's first
+// half (F x, the optional saved spectrum, the multiply by H) and its second
+// half (the inverse) are separately compiled device functions that meet only
+// through the exchange buffer, where the first half leaves F x * H in natural
+// order.  Inlined into one body, the two transforms' register allocations
+// merge and spill (~0.8 KiB per thread); as calls, each half is allocated on
+// its own and only pointers cross.  One HBM read and one write per point
+// (plus the saved spectrum), the arithmetic of FM_SPEC followed by FM_MULINV.
+template <int N, int P, class SC>
+__device__ __noinline__ void filter_half_fwd(const float2 *src, float2 *xs, const float2 *H,
+                                             float2 *buf, const float2 *tw, int lt, int active,
+                                             int conj_h) {
+  constexpr int T = N / P;
+  float2 v[P];
+#pragma unroll
+  for (int m = 0; m < P; ++m) v[m] = active ? __ldcs(src + lt + m * T) : make_float2(0.f, 0.f);
+  run_passes<N, P, -1, SC, 0, SwizzledRow, 1>(v, lt, buf, tw, SwizzledRow{});
+  // v[m] = (F x)[final_index(lt, m)]
+#pragma unroll
+  for (int m = 0; m < P; ++m) {
+    const int k = final_index<N, P, SC>(lt, m);
+    if (active && xs) __stcs(xs + k, v[m]);
+    const float2 h = __ldg(H + k);
+    v[m] = conj_h ? cmulc(v[m], h) : cmul(v[m], h);
+  }
+  __syncthreads();  // every read of the buffer by the transform is done
+#pragma unroll
+  for (int m = 0; m < P; ++m) buf[final_index<N, P, SC>(lt, m)] = v[m];
+}
+
+template <int N, int P, class SC>
+__device__ __noinline__ void filter_half_inv(float2 *buf, float2 *dst, const float2 *tw, int lt,
+                                             int active, float scale) {
+  constexpr int T = N / P;
+  float2 v[P];
+#pragma unroll
+  for (int m = 0; m < P; ++m) v[m] = buf[lt + m * T];
+  __syncthreads();  // every thread has its inputs: the transform may overwrite the buffer
+  run_passes<N, P, +1, SC, 0, SwizzledRow, 1>(v, lt, buf, tw, SwizzledRow{});
+  if (active) {
+#pragma unroll
+    for (int m = 0; m < P; ++m) __stcs(dst + final_index<N, P, SC>(lt, m), cscale(v[m], scale));
+  }
+}
+
+template <int N, int P, int TB, class SC>
+__global__ void __launch_bounds__(TB *(N / P), (65536 / (TB * (N / P) * 128)) > 0 ? 65536 / (TB * (N / P) * 128) : 1)
+filter_fwd2_kernel(FilterArgs a) {
+  constexpr int T = N / P;
+  extern __shared__ __align__(128) float2 smem[];
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int b = threadIdx.x / T;
+  const int lt = threadIdx.x - b * T;
+  float2 *buf = smem + b * N;
+  const long long ntiles = (a.batch + TB - 1) / TB;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long row = tile * TB + b;
+    const int active = row < a.batch;
+    filter_half_fwd<N, P, SC>(a.in + row * N, a.x_save ? a.x_save + row * N : nullptr, a.H, buf,
+                              a.tw, lt, active, a.conj_h);
+    __syncthreads();  // F x * H is in the buffer
+    filter_half_inv<N, P, SC>(buf, a.out + row * N, a.tw, lt, active, a.scale);
+    __syncthreads();  // the next tile rewrites the buffer
+  }
+}
+
+// One-kernel backward for 32 points per thread (N >= 8192), persistent:
+// CTA c takes rows c, c + G, c + 2G, ... (G = gridDim.x).  Per row, the first
+// half computes g_z = F g_y / N, adds conj(X_saved) * g_z into the CTA's
+// grad_H partial sums and leaves conj(H) * g_z in the exchange buffer; the
+// second half (filter_half_inv) runs F^H into grad_x.  The partial sums live
+// in tensor memory (tcgen05): each thread owns its lane and 64 columns, the
+// sums of its 32 frequencies, read and written 8 points at a time; each
+// frequency's sum runs over the CTA's rows in row order.  At the end every
+// CTA writes its sums as one row of `partial` ([G][N]), and grad_h_tree adds
+// the G rows in a fixed pairwise order, so grad_H is bitwise reproducible
+// for a given grid.
+struct FilterBwdArgs {
+  const float2 *gy;   // incoming gradient g_y
+  const float2 *xs;   // X_saved = F x
+  const float2 *H;
+  float2 *gx;         // grad_x
+  float2 *partial;    // [gridDim.x][N] per-CTA grad_H sums
+  const float2 *tw;
+  long long batch;
+  float inv_n;
+};
+
+// 16 consecutive columns of this thread's lane; the values may be used only
+// after tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]),
+        "=f"(r[7]), "=f"(r[8]), "=f"(r[9]), "=f"(r[10]), "=f"(r[11]), "=f"(r[12]), "=f"(r[13]),
+        "=f"(r[14]), "=f"(r[15])
+      : "r"(taddr));
+}
+// The loaded registers are listed as operands so that no use of them is
+// scheduled above the wait.
+__device__ __forceinline__ void tmem_wait_ld(float (&r)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+f"(r[0]), "+f"(r[1]), "+f"(r[2]), "+f"(r[3]), "+f"(r[4]), "+f"(r[5]),
+                 "+f"(r[6]), "+f"(r[7]), "+f"(r[8]), "+f"(r[9]), "+f"(r[10]), "+f"(r[11]),
+                 "+f"(r[12]), "+f"(r[13]), "+f"(r[14]), "+f"(r[15])
+               :
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16};" ::"r"(taddr),
+      "f"(r[0]), "f"(r[1]), "f"(r[2]), "f"(r[3]), "f"(r[4]), "f"(r[5]), "f"(r[6]), "f"(r[7]),
+      "f"(r[8]), "f"(r[9]), "f"(r[10]), "f"(r[11]), "f"(r[12]), "f"(r[13]), "f"(r[14]),
+      "f"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+template <int N, int P, class SC>
+__device__ __noinline__ void filter_half_bwd(const float2 *gy, const float2 *xs, const float2 *H,
+                                             float2 *buf, const float2 *tw, int lt, float inv_n,
+                                             uint32_t taddr) {
+  constexpr int T = N / P;
+  static_assert(P % 8 == 0, "partial sums move 8 points at a time");
+  float2 v[P];
+#pragma unroll
+  for (int m = 0; m < P; ++m) v[m] = __ldcs(gy + lt + m * T);
+  // this thread's saved-spectrum points into L1 while the transform runs
+#pragma unroll
+  for (int m = 0; m < P; ++m)
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(xs + final_index<N, P, SC>(lt, m)));
+  run_passes<N, P, -1, SC, 0, SwizzledRow, 1>(v, lt, buf, tw, SwizzledRow{});
+  // v[m] = (F g_y)[final_index(lt, m)]; g_z = that / N
+#pragma unroll
+  for (int m = 0; m < P; ++m) v[m] = cscale(v[m], inv_n);
+  // Chunk c: its sums' tensor-memory read and its X loads are issued
+  // together, and chunk c + 1's right after chunk c's store, so the two
+  // latencies overlap.
+  float r[16];
+  float2 x[8];
+  tmem_ld16(taddr, r);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) x[q] = __ldcs(xs + final_index<N, P, SC>(lt, q));
+#pragma unroll
+  for (int c = 0; c < P / 8; ++c) {
+    tmem_wait_ld(r);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {  // sum += conj(x) g_z
+      const float2 g = v[8 * c + q];
+      r[2 * q] = fmaf(x[q].x, g.x, fmaf(x[q].y, g.y, r[2 * q]));
+      r[2 * q + 1] = fmaf(x[q].x, g.y, fmaf(-x[q].y, g.x, r[2 * q + 1]));
+    }
+    tmem_st16(taddr + 16 * c, r);
+    if (c + 1 < P / 8) {
+      tmem_ld16(taddr + 16 * (c + 1), r);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) x[q] = __ldcs(xs + final_index<N, P, SC>(lt, 8 * (c + 1) + q));
+    }
+  }
+  tmem_wait_st();
+#pragma unroll
+  for (int m = 0; m < P; ++m) v[m] = cmulc(v[m], __ldg(H + final_index<N, P, SC>(lt, m)));
+  __syncthreads();  // every read of the buffer by the transform is done
+#pragma unroll
+  for (int m = 0; m < P; ++m) buf[final_index<N, P, SC>(lt, m)] = v[m];
+}
+
+template <int N, int P, class SC>
+__global__ void __launch_bounds__(N / P, (65536 / ((N / P) * 128)) > 0 ? 65536 / ((N / P) * 128) : 1)
+filter_bwd2_kernel(FilterBwdArgs a) {
+  constexpr int T = N / P;
+  constexpr int WARPS = T / 32;
+  static_assert(T % 128 == 0, "whole warpgroups cover the tensor-memory lanes");
+  constexpr uint32_t NCOL = (WARPS / 4) * 64 < 32 ? 32 : (WARPS / 4) * 64;  // 128 or 256
+  extern __shared__ __align__(128) float2 smem[];
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + N);
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int lt = threadIdx.x, warp = lt >> 5;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(tslot)),
+                 "r"(NCOL));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tbase = *tslot;
+  // lane quarter warp % 4 (the lanes this warp may address), 64 columns per
+  // group of four warps
+  const uint32_t taddr = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * (warp >> 2));
+  {
+    float z[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) z[i] = 0.f;
+#pragma unroll
+    for (int c = 0; c < P / 8; ++c) tmem_st16(taddr + 16 * c, z);
+    tmem_wait_st();
+  }
+  if (warp == 0 && blockIdx.x < a.batch)  // the first row's saved spectrum into L2
+    prefetch_l2_warp(a.xs + (long long)blockIdx.x * N, (long long)sizeof(float2) * N, lt);
+  for (long long row = blockIdx.x; row < a.batch; row += gridDim.x) {
+    const long long next = row + gridDim.x;
+    if (warp == 0 && next < a.batch) {  // the next row's g_y and saved spectrum into L2
+      prefetch_l2_warp(a.gy + next * N, (long long)sizeof(float2) * N, lt);
+      prefetch_l2_warp(a.xs + next * N, (long long)sizeof(float2) * N, lt);
+    }
+    filter_half_bwd<N, P, SC>(a.gy + row * N, a.xs + row * N, a.H, smem, a.tw, lt, a.inv_n,
+                              taddr);
+    __syncthreads();  // conj(H) g_z is in the buffer
+    filter_half_inv<N, P, SC>(smem, a.gx + row * N, a.tw, lt, 1, 1.0f);
+    __syncthreads();  // the next row rewrites the buffer
+  }
+  float2 *dst = a.partial + (size_t)blockIdx.x * N;
+#pragma unroll
+  for (int c = 0; c < P / 8; ++c) {
+    float r[16];
+    tmem_ld16(taddr + 16 * c, r);
+    tmem_wait_ld(r);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      dst[final_index<N, P, SC>(lt, 8 * c + q)] = make_float2(r[2 * q], r[2 * q + 1]);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(NCOL));
+}
+
 struct FilterKernel {
   const void *fn;
   int threads, tb;
@@ -144,13 +378,12 @@ static FilterKernel make_kernel() {
 
 // The kernels of one N share a radix schedule (and its twiddle tables): 32
 // points per thread from 8192 on (three passes, like the plain transform's
-// built-in), 16 below.  With 32 points both transforms of FM_FWD do not fit
-// the register budget (~0.8-1 KiB of spills per thread, written back to
-// DRAM), so from 8192 on the forward runs as FM_SPEC into the saved spectrum
-// (or into y) and FM_MULINV from there: one more HBM pass, no spills, and
-// measured faster.
+// built-in), 16 below.  With 32 points both transforms inlined into FM_FWD do
+// not fit the register budget (~0.8-1 KiB of spills per thread), so from
+// 8192 on the forward is filter_fwd2_kernel (the two halves as calls).
 struct FilterVariant {
   FilterKernel fwd, spec, mulinv;  // fwd.fn == nullptr: the two-kernel forward
+  FilterKernel bwd;                // one-kernel backward (32 points per thread), else nullptr
   KernelEntry sched;
 };
 
@@ -158,8 +391,20 @@ template <int N, int P, int TB, int... Rs>
 static FilterVariant variant() {
   using SC = Sched<Rs...>;
   FilterVariant v;
-  if constexpr (P < 32) v.fwd = make_kernel<N, P, TB, SC, FM_FWD>();
-  else v.fwd = FilterKernel{nullptr, 0, 0, 0};
+  if constexpr (P < 32) {
+    v.fwd = make_kernel<N, P, TB, SC, FM_FWD>();
+  } else {
+    v.fwd.fn = (const void *)&filter_fwd2_kernel<N, P, TB, SC>;
+    v.fwd.threads = TB * (N / P);
+    v.fwd.tb = TB;
+    v.fwd.smem = sizeof(float2) * (size_t)N * TB;
+    static_assert(P < 32 || TB == 1, "one row per CTA for the persistent backward");
+    v.bwd.fn = (const void *)&filter_bwd2_kernel<N, P, SC>;
+    v.bwd.threads = N / P;
+    v.bwd.tb = 1;
+    v.bwd.smem = sizeof(float2) * (size_t)N + 16;  // + the tensor-memory address slot
+  }
+  if constexpr (P < 32) v.bwd = FilterKernel{nullptr, 0, 0, 0};
   v.spec = make_kernel<N, P, TB, SC, FM_SPEC>();
   v.mulinv = make_kernel<N, P, TB, SC, FM_MULINV>();
   v.sched = KernelEntry{};
@@ -183,7 +428,9 @@ static bool filter_variant(int N, FilterVariant *v) {
 
 struct FilterState {
   FilterVariant v;
-  float2 *d_work = nullptr;  // grad_H reduction workspace (32-row chunk sums)
+  float2 *d_work = nullptr;  // grad_H workspace: 32-row chunk sums, or one row per CTA of
+                             // the one-kernel backward
+  int bwd_grid = 0;          // CTAs of the one-kernel backward (resident on the GPU at once)
 };
 
 void filter_destroy(fft_plan_impl *pl) {
@@ -231,7 +478,7 @@ fft_status_t fft_filter_plan(fft_plan_t *out, int N, int64_t batch) {
     return fail(FFT_ERR_ALLOC);
   }
   cudaMemset(pl->d_status, 0, sizeof(int));
-  for (const FilterKernel *k : {&v.fwd, &v.spec, &v.mulinv}) {
+  for (const FilterKernel *k : {&v.fwd, &v.spec, &v.mulinv, &v.bwd}) {
     if (k->fn && k->smem > 48 * 1024 &&
         cudaFuncSetAttribute(k->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k->smem) !=
             cudaSuccess)
@@ -240,7 +487,25 @@ fft_status_t fft_filter_plan(fft_plan_t *out, int N, int64_t batch) {
   int64_t off = 0;
   fft_status_t s = build_twiddles(pl, pass_segments(v.sched, off));
   if (s != FFT_OK) return fail(s);
-  const int64_t work = fft_filter_grad_h_workspace(N, batch);
+  int64_t work = fft_filter_grad_h_workspace(N, batch);
+  if (v.bwd.fn && batch > 0) {
+    // Resident CTAs per SM: the occupancy query reports one for any kernel
+    // that allocates tensor memory, while the hardware co-schedules as many
+    // as registers and shared memory allow (measured at 8192: two, 213 vs
+    // 270 us).  So take the forward kernel's occupancy (same threads,
+    // registers and shared memory) and cap it by the tensor-memory columns:
+    // 512 per SM, 64 per group of four warps per CTA.
+    int sms = 0, occ = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v.fwd.fn, v.fwd.threads,
+                                                      v.fwd.smem) != cudaSuccess ||
+        occ < 1)
+      return fail(FFT_ERR_CUDA);
+    const int tmem_cols = std::max(32, (v.bwd.threads / 128) * 64);
+    occ = std::min(occ, 512 / tmem_cols);
+    f->bwd_grid = (int)std::min<int64_t>((int64_t)occ * sms, batch);
+    work = std::max<int64_t>(work, (int64_t)f->bwd_grid * N * (int64_t)sizeof(float2));
+  }
   if (work > 0 && cudaMalloc(&f->d_work, (size_t)work) != cudaSuccess) {
     cudaGetLastError();
     return fail(FFT_ERR_ALLOC);
@@ -282,16 +547,16 @@ fft_status_t fft_filter_forward(fft_plan_t plan, const void *x, const void *H, v
   a.batch = pl->batch;
   a.conj_h = conj_h ? 1 : 0;
   a.scale = 1.0f / (float)pl->N;
-  if (f->v.fwd.fn) return filter_launch(f->v.fwd, a, st);
-  // two kernels: F x into X_save (or y), then y = G (F x * H) from there
   const int64_t bytes = (int64_t)sizeof(float2) * pl->N * pl->batch;
-  if (X_save) {
+  if (X_save) {  // the saved spectrum may not overlap x or y (header contract)
     const char *p = (const char *)X_save;
     for (const void *o : {x, (const void *)y}) {
       const char *q = (const char *)o;
       if (p < q + bytes && q < p + bytes) return FFT_ERR_INVALID_VALUE;
     }
   }
+  if (f->v.fwd.fn) return filter_launch(f->v.fwd, a, st);
+  // two kernels: F x into X_save (or y), then y = G (F x * H) from there
   float2 *spec = X_save ? (float2 *)X_save : (float2 *)y;
   a.out = spec;
   a.x_save = nullptr;
@@ -321,6 +586,22 @@ fft_status_t fft_filter_backward(fft_plan_t plan, const void *g_y, const void *H
       const char *p = (const char *)o;
       if (p < gx + bytes && gx < p + bytes) return FFT_ERR_INVALID_VALUE;
     }
+  }
+  if (f->v.bwd.fn) {  // one kernel, then the fixed-order tree over its per-CTA sums
+    FilterBwdArgs b{};
+    b.gy = (const float2 *)g_y;
+    b.xs = (const float2 *)X_saved;
+    b.H = (const float2 *)H;
+    b.gx = (float2 *)grad_x;
+    b.partial = f->d_work;
+    b.tw = pl->d_tw;
+    b.batch = pl->batch;
+    b.inv_n = 1.0f / (float)N;
+    void *args[] = {&b};
+    if ((s = cuda_status(launch_pdl(f->v.bwd.fn, dim3((unsigned)f->bwd_grid),
+                                    dim3(f->v.bwd.threads), f->v.bwd.smem, st, args))) != FFT_OK)
+      return s;
+    return grad_h_tree(f->d_work, (float2 *)grad_H, N, f->bwd_grid, st);
   }
   FilterArgs a{};
   a.tw = pl->d_tw;

@@ -128,6 +128,9 @@ void filter_destroy(fft_plan_impl *pl);
 fft_status_t ragged_exec(fft_plan_impl *pl, const float2 *in, float2 *out, cudaStream_t st);
 void ragged_destroy(fft_plan_impl *pl);
 void ragged_clear_choices();  // forget the ragged autotuner's choices
+// grad_H = fixed-order pairwise sum of the nchunk rows of partial (spectral.cu)
+fft_status_t grad_h_tree(float2 *partial, float2 *grad_H, int N, int64_t nchunk,
+                         cudaStream_t st);
 
 }  // namespace fftgb
 

@@ -110,6 +110,32 @@ __global__ void copy_row_kernel(const float2 *src, float2 *dst, int N) {
 
 static bool pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 
+// grad_H[k] = fixed-order pairwise sum over the nchunk rows of partial
+// ([nchunk][N], overwritten): one launch while the rows fit shared memory,
+// else level by level.
+fft_status_t grad_h_tree(float2 *partial, float2 *grad_H, int N, int64_t nchunk,
+                         cudaStream_t st) {
+  const int threads = 256;
+  const unsigned bx = (unsigned)((N + threads - 1) / threads);
+  if (nchunk <= kTreeMaxChunks) {
+    const size_t smem = sizeof(float2) * (size_t)nchunk * kTreeCols;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(grad_h_tree_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return FFT_ERR_CUDA;
+    grad_h_tree_smem_kernel<<<(unsigned)((N + kTreeCols - 1) / kTreeCols), kTreeThreads, smem, st>>>(
+        partial, grad_H, N, (int)nchunk);
+    return cuda_status(cudaGetLastError());
+  }
+  if (nchunk > 65535 * 2) return FFT_ERR_INVALID_SIZE;
+  for (int64_t h = 1; h < nchunk; h *= 2) {
+    const int64_t groups = (nchunk + 2 * h - 1) / (2 * h);
+    grad_h_tree_kernel<<<dim3(bx, (unsigned)groups), threads, 0, st>>>(partial, N, nchunk, h);
+  }
+  copy_row_kernel<<<bx, threads, 0, st>>>(partial, grad_H, N);
+  return cuda_status(cudaGetLastError());
+}
+
 }  // namespace fftgb
 
 using namespace fftgb;
@@ -159,22 +185,7 @@ fft_status_t fft_filter_grad_h(const void *X, const void *G, void *grad_H, int N
   float2 *part = (float2 *)work;
   grad_h_partial_kernel<<<dim3(bx, (unsigned)nchunk), threads, 0, st>>>(
       (const float2 *)X, (const float2 *)G, part, N, batch);
-  if (nchunk <= kTreeMaxChunks) {
-    const size_t smem = sizeof(float2) * (size_t)nchunk * kTreeCols;
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(grad_h_tree_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-      return FFT_ERR_CUDA;
-    grad_h_tree_smem_kernel<<<(unsigned)((N + kTreeCols - 1) / kTreeCols), kTreeThreads, smem, st>>>(
-        part, (float2 *)grad_H, N, (int)nchunk);
-    return cuda_status(cudaGetLastError());
-  }
-  for (int64_t h = 1; h < nchunk; h *= 2) {
-    const int64_t groups = (nchunk + 2 * h - 1) / (2 * h);
-    grad_h_tree_kernel<<<dim3(bx, (unsigned)groups), threads, 0, st>>>(part, N, nchunk, h);
-  }
-  copy_row_kernel<<<bx, threads, 0, st>>>(part, (float2 *)grad_H, N);
-  return cuda_status(cudaGetLastError());
+  return grad_h_tree(part, (float2 *)grad_H, N, nchunk, st);
 }
 
 }  // extern "C"
