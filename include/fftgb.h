@@ -365,16 +365,16 @@ fft_status_t fft_filter_grad_h(const void *X, const void *G, void *grad_H, int N
  * fft_filter_forward: y = IFFT(FFT(x) * H) (conj_h = 1: * conj(H)), inverse
  *   scaled by 1/N; if X_save is non-NULL it also receives FFT(x) (needed by
  *   the backward).  x, y, X_save: batch*N float2; H: N float2.  y may equal
- *   x; X_save may not overlap x or y (FFT_ERR_INVALID_VALUE).  N <= 4096:
- *   one kernel, one HBM round trip per row; N >= 8192: the spectrum kernel
- *   (into X_save, else into y) and the multiply-and-inverse kernel, one
- *   more pass (a single kernel holding both 32-point transforms spills).
+ *   x; X_save may not overlap x or y (FFT_ERR_INVALID_VALUE).  One kernel,
+ *   one HBM read and one write per point of y (plus X_save).
  * fft_filter_backward: with g_y = dL/dy (PyTorch convention),
  *   grad_x = IFFT(FFT(g_y) * conj(H)) = F^H(conj(H) * g_z), g_z = FFT(g_y)/N,
- *   grad_H = sum_rows conj(X_saved) * g_z  (sums over 32-row chunks in row
- *   order, then a fixed-order pairwise tree: bitwise reproducible on a given
- *   GPU).  Three kernels: g_z into grad_x's buffer, the grad_H reduction,
- *   then grad_x in place; so grad_x may not overlap g_y or X_saved
+ *   grad_H = sum_rows conj(X_saved) * g_z  (per-block sums over fixed row
+ *   sets in row order, then a fixed-order pairwise tree: bitwise
+ *   reproducible on a given GPU).  N >= 8192: one kernel (its grad_H partial
+ *   sums in tensor memory) and the tree; N <= 4096: three kernels (g_z into
+ *   grad_x's buffer, the grad_H reduction over 32-row chunks, then grad_x in
+ *   place).  grad_x may not overlap g_y or X_saved
  *   (FFT_ERR_INVALID_VALUE).
  * Device pointers, 16-byte aligned; asynchronous on stream.
  * Paper: Sec. IX-A (FFT fused with matched filtering in one kernel) and
