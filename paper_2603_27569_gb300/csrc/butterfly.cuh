@@ -38,15 +38,31 @@ __device__ __forceinline__ float2 csub(float2 a, float2 b) {
   return make_float2(a.x - b.x, a.y - b.y);
 #endif
 }
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+  return __fmul2_rn(a, make_float2(s, s));
+#else
+  return make_float2(a.x * s, a.y * s);
+#endif
+}
 
 // a * w
 __device__ __forceinline__ float2 cmul(float2 a, float2 w) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+  const float2 t = __fmul2_rn(make_float2(a.y, a.y), make_float2(w.y, w.x));
+  return __ffma2_rn(make_float2(a.x, a.x), w, make_float2(-t.x, t.y));
+#else
   return make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
+#endif
 }
 // a * conj(w)
 __device__ __forceinline__ float2 cmulc(float2 a, float2 w) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+  const float2 t = __fmul2_rn(make_float2(a.y, a.x), make_float2(w.y, w.y));
+  return __ffma2_rn(make_float2(a.x, a.y), make_float2(w.x, w.x), make_float2(t.x, -t.y));
+#else
   return make_float2(fmaf(a.x, w.x, a.y * w.y), fmaf(a.y, w.x, -a.x * w.y));
+#endif
 }
 // a * w (D = -1) or a * conj(w) (D = +1): tables hold forward roots.
 template <int D>
@@ -172,13 +188,27 @@ __device__ __forceinline__ void bfly_rot32(float2 e, float2 o, float2 &lo, float
     constexpr float q = cbig ? (float)(s / c) : (float)(c / s);
     constexpr float g = cbig ? (float)c : (float)s;
     float2 u;
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+    if constexpr (cbig) {
+      u = __ffma2_rn(make_float2(-o.y, o.x), make_float2(q, q), o);
+    } else {
+      u = __ffma2_rn(o, make_float2(q, q), make_float2(-o.y, o.x));
+    }
+#else
     if constexpr (cbig) {
       u = make_float2(fmaf(-o.y, q, o.x), fmaf(o.x, q, o.y));
     } else {
       u = make_float2(fmaf(o.x, q, -o.y), fmaf(o.y, q, o.x));
     }
+#endif
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+    // e +- g u as two packed FP32x2 FMAs (the same roundings as four scalar ones)
+    lo = __ffma2_rn(u, make_float2(g, g), e);
+    hi = __ffma2_rn(u, make_float2(-g, -g), e);
+#else
     lo = make_float2(fmaf(u.x, g, e.x), fmaf(u.y, g, e.y));
     hi = make_float2(fmaf(u.x, -g, e.x), fmaf(u.y, -g, e.y));
+#endif
   }
 }
 
@@ -218,9 +248,16 @@ __host__ __device__ constexpr bool tw_loaded(int j) {
 // a b and a conj(b) with their shared products formed once: 2 FMUL + 4 FFMA
 // for the two, against 2 x (FMUL + FFMA) x 2 for two separate products.
 __device__ __forceinline__ void cmul_pm(float2 a, float2 b, float2 &plus, float2 &minus) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+  const float2 tu = __fmul2_rn(make_float2(a.y, a.x), make_float2(b.y, b.y));
+  const float2 ab = make_float2(a.x, a.y), bb = make_float2(b.x, b.x);
+  plus = __ffma2_rn(ab, bb, make_float2(-tu.x, tu.y));
+  minus = __ffma2_rn(ab, bb, make_float2(tu.x, -tu.y));
+#else
   const float t = a.y * b.y, u = a.x * b.y;
   plus = make_float2(fmaf(a.x, b.x, -t), fmaf(a.y, b.x, u));
   minus = make_float2(fmaf(a.x, b.x, t), fmaf(a.y, b.x, -u));
+#endif
 }
 
 // Twiddle mode 1: form the rows that are not read as products of rows
