@@ -13,7 +13,10 @@
 // and |s|, o w = g u where u = o rotated by the ratio of the smaller to g
 // (|ratio| <= 1), so the pair costs 2 FFMA for u and 4 FFMA for e +- g u:
 // six instructions instead of eight (four for o w, four for the add and
-// the subtract).
+// the subtract).  On sm_100 and later the two components of every complex
+// add, FMA and product issue as one packed FP32x2 instruction (FADD2, FFMA2,
+// FMUL2) with the scalar forms' roundings, so results are bit-identical and
+// the six FMAs of a rotated butterfly pair are three instructions.
 // Twiddle mode 1 helpers (tw_loaded, cmul_pm, derive_twiddles) form a pass's
 // twiddle powers from the few table rows it reads.
 #pragma once
