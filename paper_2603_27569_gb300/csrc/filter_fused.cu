@@ -133,6 +133,9 @@ filter_kernel(FilterArgs a) {
 // merge and spill (~0.8 KiB per thread); as calls, each half is allocated on
 // its own and only pointers cross.  One HBM read and one write per point
 // (plus the saved spectrum), the arithmetic of FM_SPEC followed by FM_MULINV.
+// Launched as a resident grid (occupancy x SMs) that walks the rows; warp 0
+// asks the bulk-copy engine to prefetch the CTA's next row into L2 when a
+// row starts.
 template <int N, int P, class SC>
 __device__ __noinline__ void filter_half_fwd(const float2 *src, float2 *xs, const float2 *H,
                                              float2 *buf, const float2 *tw, int lt, int active,
@@ -182,6 +185,11 @@ filter_fwd2_kernel(FilterArgs a) {
   float2 *buf = smem + b * N;
   const long long ntiles = (a.batch + TB - 1) / TB;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long next = tile + gridDim.x;
+    if (threadIdx.x < 32 && next < ntiles) {  // the next tile's rows into L2
+      const long long rows = a.batch - next * TB < TB ? a.batch - next * TB : TB;
+      prefetch_l2_warp(a.in + next * TB * N, rows * N * (long long)sizeof(float2), threadIdx.x);
+    }
     const long long row = tile * TB + b;
     const int active = row < a.batch;
     filter_half_fwd<N, P, SC>(a.in + row * N, a.x_save ? a.x_save + row * N : nullptr, a.H, buf,
@@ -431,6 +439,7 @@ struct FilterState {
   float2 *d_work = nullptr;  // grad_H workspace: 32-row chunk sums, or one row per CTA of
                              // the one-kernel backward
   int bwd_grid = 0;          // CTAs of the one-kernel backward (resident on the GPU at once)
+  int fwd_grid = 0;          // CTAs of the one-kernel forward (32 points per thread)
 };
 
 void filter_destroy(fft_plan_impl *pl) {
@@ -501,6 +510,7 @@ fft_status_t fft_filter_plan(fft_plan_t *out, int N, int64_t batch) {
                                                       v.fwd.smem) != cudaSuccess ||
         occ < 1)
       return fail(FFT_ERR_CUDA);
+    f->fwd_grid = (int)std::min<int64_t>((int64_t)occ * sms, batch);
     const int tmem_cols = std::max(32, (v.bwd.threads / 128) * 64);
     occ = std::min(occ, 512 / tmem_cols);
     f->bwd_grid = (int)std::min<int64_t>((int64_t)occ * sms, batch);
@@ -554,6 +564,11 @@ fft_status_t fft_filter_forward(fft_plan_t plan, const void *x, const void *H, v
       const char *q = (const char *)o;
       if (p < q + bytes && q < p + bytes) return FFT_ERR_INVALID_VALUE;
     }
+  }
+  if (f->v.fwd.fn && f->fwd_grid > 0) {  // persistent: a resident grid walks the rows
+    void *args[] = {&a};
+    return cuda_status(launch_pdl(f->v.fwd.fn, dim3((unsigned)f->fwd_grid), dim3(f->v.fwd.threads),
+                                  f->v.fwd.smem, st, args));
   }
   if (f->v.fwd.fn) return filter_launch(f->v.fwd, a, st);
   // two kernels: F x into X_save (or y), then y = G (F x * H) from there

@@ -73,30 +73,50 @@ __global__ void grad_h_tree_kernel(float2 *partial, int N, int64_t nchunk, int64
   partial[c * N + k] = make_float2(a.x + b.x, a.y + b.y);
 }
 
-// The same pairwise tree in one launch: a CTA stages the partial sums of
-// kTreeCols frequencies for every chunk in shared memory, runs the levels
-// (same additions in the same order as grad_h_tree_kernel, so the result is
-// identical) and writes grad_H for its frequencies.  Used while the chunk
-// rows fit the shared memory (kTreeMaxChunks).
-constexpr int kTreeCols = 32;
+// The same pairwise tree in one launch.  A CTA owns kTreeCols frequencies.
+// Each thread loads aligned blocks of kTreeBlk consecutive chunks of one
+// frequency (all of a block's loads in flight together) and runs the tree's
+// first levels (h = 1, 2, 4) inside the block in registers; the block sums go
+// to shared memory, where the remaining levels run over blocks.  Levels h <
+// kTreeBlk only pair chunks inside an aligned block, and level kTreeBlk * hb
+// pairs block b with block b + hb exactly when chunk 8 (b + hb) exists, so
+// the additions and their order are those of grad_h_tree_kernel and the
+// result is identical.  Used while the block sums fit the shared memory
+// (kTreeMaxChunks).
+constexpr int kTreeCols = 16;
 constexpr int kTreeThreads = 256;
-constexpr int64_t kTreeMaxChunks = 768;  // 768 x 32 x 8 B = 192 KiB
+constexpr int kTreeBlk = 8;
+constexpr int64_t kTreeMaxChunks = 4096;  // 512 blocks x 16 x 8 B = 64 KiB
 
 __global__ void __launch_bounds__(kTreeThreads) grad_h_tree_smem_kernel(const float2 *partial,
                                                                        float2 *out, int N,
                                                                        int nchunk) {
-  extern __shared__ float2 tree[];  // [nchunk][kTreeCols]
+  extern __shared__ float2 tree[];  // [nblk][kTreeCols] block sums
   const int k0 = blockIdx.x * kTreeCols;
   const int f = threadIdx.x % kTreeCols, lane = threadIdx.x / kTreeCols;
   constexpr int kLanes = kTreeThreads / kTreeCols;
   const bool on = k0 + f < N;
-  for (int c = lane; c < nchunk; c += kLanes)
-    tree[c * kTreeCols + f] = on ? partial[(int64_t)c * N + k0 + f] : make_float2(0.f, 0.f);
+  const int nblk = (nchunk + kTreeBlk - 1) / kTreeBlk;
+  for (int bl = lane; bl < nblk; bl += kLanes) {
+    const int c0 = bl * kTreeBlk;
+    float2 v[kTreeBlk];
+#pragma unroll
+    for (int i = 0; i < kTreeBlk; ++i)
+      v[i] = on && c0 + i < nchunk ? __ldcs(partial + (int64_t)(c0 + i) * N + k0 + f)
+                                   : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int h = 1; h < kTreeBlk; h *= 2) {
+#pragma unroll
+      for (int i = 0; i + h < kTreeBlk; i += 2 * h)
+        if (c0 + i + h < nchunk) v[i] = make_float2(v[i].x + v[i + h].x, v[i].y + v[i + h].y);
+    }
+    tree[bl * kTreeCols + f] = v[0];
+  }
   __syncthreads();
-  for (int h = 1; h < nchunk; h *= 2) {
-    for (int c = 2 * h * lane; c + h < nchunk; c += 2 * h * kLanes) {
-      const float2 a = tree[c * kTreeCols + f], b = tree[(c + h) * kTreeCols + f];
-      tree[c * kTreeCols + f] = make_float2(a.x + b.x, a.y + b.y);
+  for (int h = 1; h < nblk; h *= 2) {
+    for (int b = 2 * h * lane; b + h < nblk; b += 2 * h * kLanes) {
+      const float2 a = tree[b * kTreeCols + f], c = tree[(b + h) * kTreeCols + f];
+      tree[b * kTreeCols + f] = make_float2(a.x + c.x, a.y + c.y);
     }
     __syncthreads();
   }
@@ -118,7 +138,8 @@ fft_status_t grad_h_tree(float2 *partial, float2 *grad_H, int N, int64_t nchunk,
   const int threads = 256;
   const unsigned bx = (unsigned)((N + threads - 1) / threads);
   if (nchunk <= kTreeMaxChunks) {
-    const size_t smem = sizeof(float2) * (size_t)nchunk * kTreeCols;
+    const size_t smem =
+        sizeof(float2) * (size_t)((nchunk + kTreeBlk - 1) / kTreeBlk) * kTreeCols;
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(grad_h_tree_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)

@@ -103,11 +103,12 @@ def test_fft_autograd_uses_the_adjoint(N, inverse):
     assert rel(g, want) <= TOL_GRAD
 
 
-@pytest.mark.parametrize("batch", [1, 33, 32 * 700, 32 * 800 + 5])
+@pytest.mark.parametrize("batch", [1, 33, 32 * 700 + 17, 32 * 4096 + 5])
 def test_grad_h_reduction_both_tree_forms(batch):
     # grad_H = sum_rows conj(X) * G: 32-row chunk sums, then a pairwise tree
-    # over the chunks (one launch in shared memory up to 768 chunks, level by
-    # level above); checked against the FP64 sum and bitwise run to run
+    # over the chunks (one launch, 8-chunk blocks in registers and the rest in
+    # shared memory, up to 4096 chunks; level by level above); checked against
+    # the FP64 sum and bitwise run to run
     N = 64
     X = synth.gaussian((batch, N), seed=batch)
     G = synth.gaussian((batch, N), seed=batch + 1)
