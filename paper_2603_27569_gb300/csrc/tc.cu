@@ -51,10 +51,11 @@ struct TcArgs {
   const float2 *in;
   float2 *out;
   const float2 *tw;       // N = 16384: the radix-4 tail's table (stride 4096, radix 4)
-  const float2 *twx;      // exchange twiddles in TMEM-row order: [stage][j][row]
+  const float2 *twx;      // exchange twiddle factors: W_256^{j2 j} [j][j2], W_4096^{j2 k} [j2][k]
   const uint4 *bimg;      // this direction's G image: hi plane, lo plane (2 KiB each)
   int *status;            // FFT_ERR_TIMEOUT if an MMA completion wait ran out
   long long batch;
+  long long ahead;        // one-group-per-CTA grids: resident CTAs (occupancy x SMs)
   float scale;
 };
 
@@ -81,7 +82,7 @@ struct TcCfg<4096> {
 };
 template <>
 struct TcCfg<16384> {
-  static constexpr int S = 3, TAIL = 4, TB = 1, NW = 8, LBO = 144, SBO = 592, MINB = 1;
+  static constexpr int S = 3, TAIL = 4, TB = 1, NW = 16, LBO = 144, SBO = 592, MINB = 1;
   static constexpr bool PERSIST = true;
   static constexpr unsigned long long R0 = 0x8539064712ull, R1 = 0x4130576289ull,
                                       R2 = 0x9876543210ull;
@@ -205,15 +206,19 @@ __device__ __forceinline__ void tc_exchange(const uint32_t (&r)[32], int m, uint
   const int j2 = base >> IB;                  // the next stage's point index
   const int m2 = tc_row<RN, NBITS>((b << IB) | (base & (NB - 1)));
   const int off = tc_rowoff<C::SBO>(m2) + (j2 >> 2) * C::LBO + (j2 & 3) * 4;
-  // The next pass's twiddle W_{256 p}^{j2 (j p + k)} of this row's output j,
-  // from a table laid out [stage][j][row]: a warp's 32 rows read 256
-  // contiguous bytes per j.
-  constexpr int ROWS = C::TB * NB;
-  const float2 *twp = twx + (s * 16) * ROWS + m;
+  // The next pass's twiddle W_{256 p}^{j2 (j p + k)} of this row's output j
+  // is W_256^{j2 j} (times W_4096^{j2 k} after stage 1, where p = 16; k = 0
+  // after stage 0): two 16 x 16 tables of 2 KiB that stay in L1.  A warp's
+  // j2 values lie in 0..15, so each j reads one 128-byte line.
+  const float2 *tj = twx + j2;
+  float2 aw = make_float2(1.f, 0.f);
+  if constexpr (s > 0) aw = __ldg(twx + 256 + j2 * 16 + k);
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
     float2 x = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
-    x = cmul_dir<D>(x, __ldg(twp + j * ROWS));
+    float2 w = __ldg(tj + 16 * j);
+    if constexpr (s > 0) w = cmul(aw, w);
+    x = cmul_dir<D>(x, w);
     uint32_t hi, lo;
     split2<PREC>(x.x, x.y, hi, lo);
     const int oj = off + tc_rowoff<C::SBO>(tc_row<RN, NBITS>(j * p));
@@ -232,7 +237,9 @@ struct TcSmem {
 };
 
 // A CTA transforms groups of TB rows: one group, or (PERSIST) every
-// gridDim.x-th group from blockIdx.x.
+// gridDim.x-th group from blockIdx.x.  A one-group CTA first has the group
+// one resident wave ahead (blockIdx.x + occupancy x SMs) prefetched into L2,
+// so the CTA that starts when this wave retires reads its rows from L2.
 template <int N, int D, int PREC>
 __global__ void __launch_bounds__(TcCfg<N>::NW * 32, TcCfg<N>::MINB)
 tc_kernel(TcArgs a) {
@@ -271,6 +278,12 @@ tc_kernel(TcArgs a) {
   unsigned mph = 0;  // completed phases of the MMA mbarrier
   for (long long grp = blockIdx.x; grp < ngroups; grp += C::PERSIST ? gridDim.x : ngroups) {
     const long long row0 = grp * C::TB;
+    if (!C::PERSIST && warp == 0 && grp + a.ahead < ngroups) {
+      // the group that the CTA one resident wave later will load, into L2
+      const long long nxt = grp + a.ahead;
+      const long long rows = min((long long)C::TB, a.batch - nxt * C::TB);
+      prefetch_l2_warp(a.in + nxt * C::TB * N, rows * N * (long long)sizeof(float2), lane);
+    }
     if (C::PERSIST && warp == 0 && grp + gridDim.x < ngroups) {
       // the next group's rows into L2 while this one runs (bulk prefetch)
       const long long nxt = grp + gridDim.x;
@@ -371,18 +384,23 @@ tc_kernel(TcArgs a) {
           }
         }
       } else {
-        // radix-4 tail (stride 4096): this thread's tiles g + 2v (v = 0..3)
+        // radix-4 tail (stride 4096): tiles g + 2v (v = 0..3, g = g4 & 1)
         // hold butterflies k + 256 v of the last TC stage (identity rows),
         // whose outputs j are the four points of radix-4 butterfly 256 j + k.
-        static_assert(N == 16384 && TPT == 4 && NW == 8, "tail mapping");
-        const int k = 128 * g4 + 32 * q4 + lane;
+        // The warps that share a lane quarter split the tile parities g and,
+        // with 16 warps, the four column chunks jc (two each).
+        static_assert(N == 16384 && ((NW == 8 && TPT == 4) || (NW == 16 && TPT == 2)),
+                      "tail mapping");
+        constexpr int NJC = 4 / (NW / 8);
+        const int g = g4 & 1, jc0 = (g4 >> 1) * NJC;
+        const int k = 128 * g + 32 * q4 + lane;
         const float2 *tw3 = a.tw;  // W_16384^{v it}: entry (v - 1) * 4096 + it
 #pragma unroll 1
-        for (int jc = 0; jc < 4; ++jc) {
+        for (int jc = jc0; jc < jc0 + NJC; ++jc) {
           uint32_t r[4][8];
 #pragma unroll
           for (int v = 0; v < 4; ++v)
-            tc_ld8(tbase + ((uint32_t)(32 * q4) << 16) + 32 * (g4 + 2 * v) + 8 * jc, r[v]);
+            tc_ld8(tbase + ((uint32_t)(32 * q4) << 16) + 32 * (g + 2 * v) + 8 * jc, r[v]);
           tc_wait_ld();
 #pragma unroll
           for (int jj = 0; jj < 4; ++jj) {
@@ -443,23 +461,24 @@ __global__ void tc_gen_bimg(uint16_t *img) {
   }
 }
 
-// Exchange twiddles in TMEM-row order: out[(s * 16 + j) * ROWS + m] = the
-// twiddle that output j of the butterfly in row m of stage s takes into stage
-// s + 1, W_{256 p}^{j2 (j p + k)} (p = 16^s; butterfly i = p u + k, j2 = its
-// next point index), forward sign (the kernels conjugate for the inverse),
-// from the exact integer exponent in FP64, rounded to FP32.
-template <int N>
+// Exchange twiddle factors, forward sign (the kernels conjugate for the
+// inverse), each from its exact integer exponent in FP64, rounded to FP32:
+// out[16 j + j2] = W_256^{j2 j} and out[256 + 16 j2 + k] = W_4096^{j2 k}
+// (j, j2, k < 16).  The twiddle W_{256 p}^{j2 (j p + k)} that output j of a
+// butterfly (offset k < p in its stride-p group) takes into the next stage
+// is their product: p = 1 (k = 0) after stage 0, p = 16 after stage 1.
+constexpr int kTcTwx = 512;
 __global__ void tc_gen_twx(float2 *out) {
-  using C = TcCfg<N>;
-  constexpr int NB = N / 16, IB = ilog2(NB), ROWS = C::TB * NB, NBITS = ilog2(ROWS);
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (C::S - 1) * 16 * ROWS) return;
-  const int s = idx / (16 * ROWS), j = (idx / ROWS) % 16, m = idx % ROWS;
-  const int v = s == 0 ? tc_unrow<C::R0, NBITS>(m) : tc_unrow<C::R1, NBITS>(m);
-  const int p = s == 0 ? 1 : 16, LP = 4 * s;
-  const int i = v & (NB - 1), k = i & (p - 1), u = i >> LP;
-  const int j2 = ((u << (LP + 4)) | k) >> IB;
-  const long long M = 256LL * p, e = ((long long)j2 * (j * p + k)) % M;
+  if (idx >= kTcTwx) return;
+  long long M, e;
+  if (idx < 256) {
+    M = 256;
+    e = (long long)((idx >> 4) * (idx & 15)) % M;
+  } else {
+    M = 4096;
+    e = (long long)(((idx - 256) >> 4) * (idx & 15)) % M;
+  }
   double sn, cs;
   sincospi(-2.0 * (double)e / (double)M, &sn, &cs);
   out[idx] = make_float2(__double2float_rn(cs), __double2float_rn(sn));
@@ -467,25 +486,17 @@ __global__ void tc_gen_twx(float2 *out) {
 
 struct TcState {
   uint16_t *d_bimg = nullptr;  // G images, both directions (8 KiB)
-  float2 *d_twx = nullptr;     // exchange twiddles in TMEM-row order
+  float2 *d_twx = nullptr;     // exchange twiddle factors (kTcTwx entries)
   const void *fn = nullptr;
   int threads = 0, tb = 0;
   size_t smem = 0;
   bool persist = false;
-  int64_t twx_count = 0;
-  const void *gen_twx = nullptr;
   int64_t grid_cap = 0;  // CTAs per launch: occupancy x SMs when persistent
+  int64_t resident = 0;  // occupancy x SMs
 };
-
-template <int N>
-static int64_t twx_count() {
-  return (int64_t)(TcCfg<N>::S - 1) * 16 * TcCfg<N>::TB * (N / 16);
-}
 
 template <int N, int PREC>
 static void pick(TcState *st, int dir) {
-  st->twx_count = twx_count<N>();
-  st->gen_twx = (const void *)&tc_gen_twx<N>;
   st->fn = dir < 0 ? (const void *)&tc_kernel<N, -1, PREC> : (const void *)&tc_kernel<N, +1, PREC>;
   st->threads = TcCfg<N>::NW * 32;
   st->tb = TcCfg<N>::TB;
@@ -521,7 +532,8 @@ fft_status_t tc_plan(fft_plan_impl *pl) {
           cudaSuccess || occ < 1)
     return FFT_ERR_CUDA;
   st->grid_cap = st->persist ? (int64_t)occ * sms : 0x7fffffffLL;
-  // The TC stages take their twiddles from the per-row tables (d_twx); only
+  st->resident = (int64_t)occ * sms;
+  // The TC stages take their twiddles from the factor tables (d_twx); only
   // N = 16384's radix-4 tail (stride 4096) reads a pass table.
   std::vector<TwSeg> segs;
   if (pl->N == 16384) {
@@ -537,18 +549,13 @@ fft_status_t tc_plan(fft_plan_impl *pl) {
   fft_status_t s = build_twiddles(pl, segs);
   if (s != FFT_OK) return s;
   if (cudaMalloc(&st->d_bimg, 2 * 4096) != cudaSuccess ||
-      cudaMalloc(&st->d_twx, sizeof(float2) * (size_t)st->twx_count) != cudaSuccess) {
+      cudaMalloc(&st->d_twx, sizeof(float2) * (size_t)kTcTwx) != cudaSuccess) {
     cudaGetLastError();
     return FFT_ERR_ALLOC;
   }
   if (pl->precision == FFT_PREC_FP16X2) tc_gen_bimg<FFT_PREC_FP16X2><<<1, 1024>>>(st->d_bimg);
   else tc_gen_bimg<FFT_PREC_BF16X2><<<1, 1024>>>(st->d_bimg);
-  {
-    void *args[] = {&st->d_twx};
-    const unsigned blocks = (unsigned)((st->twx_count + 255) / 256);
-    if (cudaLaunchKernel(st->gen_twx, dim3(blocks), dim3(256), args, 0, 0) != cudaSuccess)
-      return FFT_ERR_CUDA;
-  }
+  tc_gen_twx<<<(kTcTwx + 255) / 256, 256>>>(st->d_twx);
   if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
     return FFT_ERR_CUDA;
   pl->path = FFT_PATH_TENSORCORE;
@@ -568,6 +575,7 @@ fft_status_t tc_exec(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t r
   a.twx = st->d_twx;
   a.status = pl->d_status;
   a.batch = rows;
+  a.ahead = st->resident;
   a.scale = pl->scale;
   const int64_t groups = (rows + st->tb - 1) / st->tb;
   if (!st->persist && groups > st->grid_cap) return FFT_ERR_INVALID_SIZE;
