@@ -92,6 +92,9 @@ typedef enum {
 #define FFT_PATH_TENSORCORE 4  /* split-precision tensor-core radix-16 DFT    */
 #define FFT_PATH_FILTER 5      /* fused spectral filter (fft_filter_plan)     */
 #define FFT_PATH_COLUMNS 6     /* strided column transforms (fft_plan_columns) */
+#define FFT_PATH_TMEM_HALVES 7 /* N = 32768 in one HBM pass: a radix-2 split into
+                                  two 16384-point halves on one SM, one half held
+                                  in tensor memory while the other transforms    */
 
 /* What a plan chose; filled by fft_plan_info(). */
 typedef struct {
@@ -116,7 +119,8 @@ typedef struct {
 
 /* One compiled execution configuration (see fft_list_configs). */
 typedef struct {
-    int path;               /* FFT_PATH_SINGLE_CTA or FFT_PATH_FOURSTEP          */
+    int path;               /* FFT_PATH_SINGLE_CTA, FFT_PATH_FOURSTEP or
+                               FFT_PATH_TMEM_HALVES (N = 32768)                 */
     int points_per_thread;  /* complex points each thread keeps in registers    */
     int transforms_per_cta; /* rows per CTA (single-CTA path)                    */
     int threads_per_cta;

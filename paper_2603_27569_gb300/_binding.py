@@ -25,6 +25,7 @@ __all__ = [
     "fft_filter_forward", "fft_filter_backward", "FFT_PATH_FILTER",
     "PlanInfo", "Config", "EXPORTED_SYMBOLS", "fft_list_configs", "fft_plan_config",
     "fft_fourstep_noalloc", "FFT_NOALLOC_MAX_POINTS", "fft_plan_columns", "FFT_PATH_COLUMNS",
+    "FFT_PATH_TMEM_HALVES",
     "fft_ragged_class_config", "FFT_FLAG_RAGGED_AUTOTUNE", "fft_ragged_list_configs",
     "fft_ragged_choose",
 ]
@@ -42,6 +43,7 @@ FFT_FLAG_RAGGED_AUTOTUNE = 0x20
 FFT_PATH_SINGLE_CTA, FFT_PATH_FOURSTEP, FFT_PATH_RAGGED, FFT_PATH_TENSORCORE = 1, 2, 3, 4
 FFT_PATH_FILTER = 5
 FFT_PATH_COLUMNS = 6
+FFT_PATH_TMEM_HALVES = 7
 FFT_NOALLOC_MAX_POINTS = 2097152
 
 STATUS = {

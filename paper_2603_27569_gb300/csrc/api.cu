@@ -29,6 +29,7 @@
 #include "cluster.cuh"
 #include "halfio.cuh"
 #include "staged.cuh"
+#include "tmem2.cuh"
 #include "plan.h"
 
 namespace fftgb {
@@ -71,6 +72,17 @@ const KernelEntry *find_split(int N, int K, int P, const int *radix, int npass, 
   for (const auto &e : kernel_registry()) {
     if (e.kind != KIND_SPLIT || e.N != N || e.split != K || e.P != P || e.npass != npass ||
         e.twm != twm)
+      continue;
+    bool same = true;
+    for (int i = 0; i < npass; ++i) same = same && e.radix[i] == radix[i];
+    if (same) return &e;
+  }
+  return nullptr;
+}
+
+const KernelEntry *find_tmem2(int N, int P, const int *radix, int npass, int twm) {
+  for (const auto &e : kernel_registry()) {
+    if (e.kind != KIND_TMEM2 || e.N != N || e.P != P || e.npass != npass || e.twm != twm)
       continue;
     bool same = true;
     for (int i = 0; i < npass; ++i) same = same && e.radix[i] == radix[i];
@@ -306,6 +318,27 @@ static fft_status_t launch_split(const KernelEntry *k, int dir, const float2 *in
   return FFT_OK;
 }
 
+static fft_status_t launch_tmem2(const KernelEntry *k, int dir, const float2 *in, float2 *out,
+                                 const float2 *tw, const float2 *tw_n, int64_t rows, float scale,
+                                 int64_t grid_cap, int *status, cudaStream_t st) {
+  if (rows <= 0) return FFT_OK;
+  Tmem2Args a;
+  a.in = in;
+  a.out = out;
+  a.tw = tw;
+  a.tw_n = tw_n;
+  a.batch = rows;
+  a.scale = scale;
+  a.status = status;
+  a.out32 = ((uintptr_t)out & 31) == 0;
+  const int64_t grid = grid_cap > 0 && grid_cap < rows ? grid_cap : rows;
+  if (grid > 0x7fffffffLL) return FFT_ERR_INVALID_SIZE;
+  void *args[] = {&a};
+  FFTGB_CUDA(launch_pdl(k->fn[dir > 0 ? 1 : 0], dim3((unsigned)grid), dim3(k->threads), k->smem,
+                        st, args));
+  return FFT_OK;
+}
+
 fft_status_t launch_column(const KernelEntry *k, int dir, const ColumnArgs &ca,
                            cudaStream_t st) {
   const int64_t grid = ca.nmat * (ca.ncols / k->TB);
@@ -364,6 +397,11 @@ static fft_status_t launch_fourstep_l2(fft_plan_impl *pl, const float2 *in, floa
 fft_status_t exec_rows(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t rows,
                        cudaStream_t st) {
   if (rows <= 0) return FFT_OK;
+  if (pl->path == FFT_PATH_TMEM_HALVES) {
+    return launch_tmem2(pl->k_single, pl->direction, in, out, pl->d_tw + pl->tw_single,
+                        pl->d_tw + pl->tw_big, rows, pl->scale, pl->grid_ctas, pl->d_status,
+                        st);
+  }
   if (pl->path == FFT_PATH_SINGLE_CTA && pl->k_single->kind == KIND_SPLIT) {
     return launch_split(pl->k_single, pl->direction, in, out, pl->d_tw + pl->tw_single,
                         pl->d_tw + pl->tw_big, rows, pl->scale, pl->grid_ctas / pl->k_single->split,
@@ -580,11 +618,11 @@ static fft_status_t plan_fourstep(fft_plan_impl *pl, int want_n1, int l2_rows) {
 
 static fft_status_t plan_single(fft_plan_impl *pl, const KernelEntry *k, int ctas_per_sm) {
   if (!k) return FFT_ERR_NOT_SUPPORTED;
-  pl->path = FFT_PATH_SINGLE_CTA;
+  pl->path = k->kind == KIND_TMEM2 ? FFT_PATH_TMEM_HALVES : FFT_PATH_SINGLE_CTA;
   pl->k_single = k;
   fft_status_t s = ensure_smem_attr(k);
   if (s != FFT_OK) return s;
-  if (k->kind == KIND_STAGED) ctas_per_sm = 1;  // one resident CTA per SM by design
+  if (k->kind == KIND_STAGED || k->kind == KIND_TMEM2) ctas_per_sm = 1;  // one per SM by design
   pl->ctas_per_sm = k->kind == KIND_SPLIT ? -1 : ctas_per_sm;
   pl->grid_ctas = k->kind == KIND_SPLIT ? k->split * resident_clusters(k)  // persistent clusters
                   : ctas_per_sm != 0   ? persistent_grid(k, ctas_per_sm)
@@ -592,6 +630,16 @@ static fft_status_t plan_single(fft_plan_impl *pl, const KernelEntry *k, int cta
   int64_t off = 0;
   pl->tw_single = 0;
   auto segs = pass_segments(*k, off);
+  if (k->kind == KIND_TMEM2) {  // + W_N^t, t < threads, the split's per-thread root
+    TwSeg g;
+    g.offset = off;
+    g.count = k->threads;
+    g.kind = 1;
+    g.p = g.r = 0;
+    g.M = pl->N;
+    pl->tw_big = off;
+    segs.push_back(g);
+  }
   if (k->kind == KIND_SPLIT) {  // + W_N^{r k2} at (r - 1) H + k2 for the cluster combine
     TwSeg g;
     g.offset = off;
@@ -655,19 +703,22 @@ static fft_status_t plan_common(fft_plan_t *out, int N, int64_t batch, int direc
   if (cfg && (cfg->l2_chunk_rows < 0 || cfg->l2_chunk_rows > kMaxL2Rows ||
               (cfg->l2_chunk_rows > 0 && cfg->path != FFT_PATH_FOURSTEP)))
     return FFT_ERR_INVALID_VALUE;
-  // Beyond one CTA's reach (N > 16384): a built-in cluster configuration
-  // (a row on a cluster of CTAs, one HBM pass) where one exists and was
-  // measured faster, else the two-phase four-step (synthesis rule 3 of
-  // Sec. IV-D, one level: N = n1 * n2, n2 <= 256, n1 <= 4096).
+  // Beyond one CTA's reach (N > 16384): a built-in one-pass configuration
+  // where one exists and was measured faster (a row on one SM with half of
+  // it in tensor memory, or on a cluster of CTAs), else the two-phase
+  // four-step (synthesis rule 3 of Sec. IV-D, one level: N = n1 * n2,
+  // n2 <= 256, n1 <= 4096).
   const KernelEntry *big_default = nullptr;
   if (N > kMaxSingleN) {
     if (precision != FFT_PREC_FP32 || (flags & FFT_FLAG_FORCE_SINGLE_CTA))
       return FFT_ERR_NOT_SUPPORTED;
-    const bool split = cfg && cfg->path == FFT_PATH_SINGLE_CTA && cfg->cluster_split > 0;
+    const bool split = cfg && ((cfg->path == FFT_PATH_SINGLE_CTA && cfg->cluster_split > 0) ||
+                               cfg->path == FFT_PATH_TMEM_HALVES);
     if (cfg && cfg->path != FFT_PATH_FOURSTEP && !split) return FFT_ERR_NOT_SUPPORTED;
     if (!cfg && !(flags & FFT_FLAG_FORCE_FOURSTEP)) {
       for (const auto &e : kernel_registry())
-        if (e.kind == KIND_SPLIT && e.N == N && e.is_default) big_default = &e;
+        if ((e.kind == KIND_SPLIT || e.kind == KIND_TMEM2) && e.N == N && e.is_default)
+          big_default = &e;
     }
     if (!split && !big_default) flags |= FFT_FLAG_FORCE_FOURSTEP;
   }
@@ -702,6 +753,10 @@ static fft_status_t plan_common(fft_plan_t *out, int N, int64_t batch, int direc
     if (cfg) {
       if (cfg->path == FFT_PATH_FOURSTEP) {
         s = plan_fourstep(pl, cfg->n1, cfg->l2_chunk_rows);
+      } else if (cfg->path == FFT_PATH_TMEM_HALVES) {
+        const KernelEntry *k = find_tmem2(N, cfg->points_per_thread, cfg->radix,
+                                          cfg->num_passes, cfg->twiddle_mode);
+        s = k ? plan_single(pl, k, -1) : FFT_ERR_NOT_SUPPORTED;
       } else if (cfg->path == FFT_PATH_SINGLE_CTA) {
         const KernelEntry *k =
             cfg->cluster_split > 0
@@ -810,6 +865,20 @@ int fft_list_configs(int N, fft_config_t *out, int capacity) {
     c.twiddle_mode = e.twm;
     c.cluster_split = e.split;
     c.ctas_per_sm = -1;
+    emit(c);
+  }
+  for (const auto &e : kernel_registry()) {
+    if (e.kind != KIND_TMEM2 || e.N != N) continue;
+    fft_config_t c;
+    memset(&c, 0, sizeof(c));
+    c.path = FFT_PATH_TMEM_HALVES;
+    c.points_per_thread = e.P;
+    c.transforms_per_cta = 1;
+    c.threads_per_cta = e.threads;
+    c.num_passes = e.npass;
+    for (int i = 0; i < 8; ++i) c.radix[i] = e.radix[i];
+    c.twiddle_mode = e.twm;
+    c.ctas_per_sm = 1;
     emit(c);
   }
   for (const auto &e : kernel_registry()) {
@@ -1060,7 +1129,8 @@ fft_status_t fft_plan_info(fft_plan_t plan, fft_plan_info_t *info) {
   info->precision = pl->precision;
   info->path = pl->path;
   info->scratch_bytes = pl->scratch_bytes;
-  const KernelEntry *k = pl->path == FFT_PATH_SINGLE_CTA ? pl->k_single
+  const bool one = pl->path == FFT_PATH_SINGLE_CTA || pl->path == FFT_PATH_TMEM_HALVES;
+  const KernelEntry *k = one                             ? pl->k_single
                          : pl->path == FFT_PATH_FOURSTEP ? (pl->k_l2 ? pl->k_l2 : pl->k_col1)
                          : pl->path == FFT_PATH_COLUMNS  ? pl->k_col2
                                                          : nullptr;
@@ -1073,7 +1143,7 @@ fft_status_t fft_plan_info(fft_plan_t plan, fft_plan_info_t *info) {
   }
   info->n1 = pl->n1;
   info->n2 = pl->n2;
-  info->twiddle_mode = pl->path == FFT_PATH_SINGLE_CTA ? pl->k_single->twm : 0;
+  info->twiddle_mode = one ? pl->k_single->twm : 0;
   info->grid_ctas = (int)pl->grid_ctas;
   info->tma_slabs = pl->path == FFT_PATH_SINGLE_CTA ? pl->k_single->slabs : 0;
   info->cluster_split = pl->path == FFT_PATH_SINGLE_CTA ? pl->k_single->split : 0;

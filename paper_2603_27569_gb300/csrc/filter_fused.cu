@@ -28,6 +28,7 @@
 
 #include "plan.h"
 #include "stockham.cuh"
+#include "tmem.cuh"
 
 extern "C" int64_t fft_filter_grad_h_workspace(int N, int64_t batch);
 extern "C" fft_status_t fft_filter_grad_h(const void *X, const void *G, void *grad_H, int N,
@@ -221,40 +222,6 @@ struct FilterBwdArgs {
   long long batch;
   float inv_n;
 };
-
-// 16 consecutive columns of this thread's lane; the values may be used only
-// after tmem_wait_ld().
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15}, [%16];"
-      : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]),
-        "=f"(r[7]), "=f"(r[8]), "=f"(r[9]), "=f"(r[10]), "=f"(r[11]), "=f"(r[12]), "=f"(r[13]),
-        "=f"(r[14]), "=f"(r[15])
-      : "r"(taddr));
-}
-// The loaded registers are listed as operands so that no use of them is
-// scheduled above the wait.
-__device__ __forceinline__ void tmem_wait_ld(float (&r)[16]) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;"
-               : "+f"(r[0]), "+f"(r[1]), "+f"(r[2]), "+f"(r[3]), "+f"(r[4]), "+f"(r[5]),
-                 "+f"(r[6]), "+f"(r[7]), "+f"(r[8]), "+f"(r[9]), "+f"(r[10]), "+f"(r[11]),
-                 "+f"(r[12]), "+f"(r[13]), "+f"(r[14]), "+f"(r[15])
-               :
-               : "memory");
-}
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&r)[16]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15,%16};" ::"r"(taddr),
-      "f"(r[0]), "f"(r[1]), "f"(r[2]), "f"(r[3]), "f"(r[4]), "f"(r[5]), "f"(r[6]), "f"(r[7]),
-      "f"(r[8]), "f"(r[9]), "f"(r[10]), "f"(r[11]), "f"(r[12]), "f"(r[13]), "f"(r[14]),
-      "f"(r[15])
-      : "memory");
-}
-__device__ __forceinline__ void tmem_wait_st() {
-  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-}
 
 template <int N, int P, class SC>
 __device__ __noinline__ void filter_half_bwd(const float2 *gy, const float2 *xs, const float2 *H,

@@ -9,6 +9,7 @@
 #include "registry.h"
 #include "staged.cuh"
 #include "stockham.cuh"
+#include "tmem2.cuh"
 
 namespace fftgb {
 
@@ -71,6 +72,23 @@ inline KernelEntry splitk_entry() {
   e.split = K;
   e.fn[0] = (const void *)&splitk_kernel<N, K, P, -1, SC, TWM>;
   e.fn[1] = (const void *)&splitk_kernel<N, K, P, +1, SC, TWM>;
+  return e;
+}
+
+template <int N, int P, int TWM, int DEF, class SC>
+inline KernelEntry tmem2_entry() {
+  KernelEntry e{};
+  e.kind = KIND_TMEM2;
+  e.N = N;
+  e.P = P;
+  e.TB = 1;
+  e.threads = (N / 2) / P;
+  e.smem = tmem2_smem_bytes<N>();
+  fill_radix<SC>(e);
+  e.is_default = DEF;
+  e.twm = TWM;
+  e.fn[0] = (const void *)&tmem2_kernel<N, P, -1, SC, TWM>;
+  e.fn[1] = (const void *)&tmem2_kernel<N, P, +1, SC, TWM>;
   return e;
 }
 
@@ -152,6 +170,14 @@ inline KernelEntry fourstep_l2_entry() {
       ::fftgb::splitk_entry<N, K, P, 0, DEF == 1, ::fftgb::Sched<__VA_ARGS__>>()); \
   static ::fftgb::Registrar FFTGB_CAT(fftgb_reg_, __COUNTER__)(              \
       ::fftgb::splitk_entry<N, K, P, 1, DEF == 2, ::fftgb::Sched<__VA_ARGS__>>())
+// FFTGB_TMEM2(N, P, is_default, radices of N/2...): a row of N points on one
+// SM with one half in tensor memory, both twiddle modes (is_default as for
+// FFTGB_STOCKHAM).
+#define FFTGB_TMEM2(N, P, DEF, ...)                                          \
+  static ::fftgb::Registrar FFTGB_CAT(fftgb_reg_, __COUNTER__)(              \
+      ::fftgb::tmem2_entry<N, P, 0, DEF == 1, ::fftgb::Sched<__VA_ARGS__>>()); \
+  static ::fftgb::Registrar FFTGB_CAT(fftgb_reg_, __COUNTER__)(              \
+      ::fftgb::tmem2_entry<N, P, 1, DEF == 2, ::fftgb::Sched<__VA_ARGS__>>())
 // FFTGB_HALF(N, P, TB, twiddle mode, radices...): 16-bit-storage kernels,
 // FP16 pairs (variant 0) and BF16 pairs (variant 1).
 #define FFTGB_HALF(N, P, TB, TWM, ...)                                       \

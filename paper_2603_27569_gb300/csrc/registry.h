@@ -14,7 +14,8 @@ enum KernelKind {
   KIND_STAGED = 3,
   KIND_SPLIT = 4,       // a row on a cluster of `split` CTAs (cluster.cuh)
   KIND_HALFIO = 5,      // FP16 storage, FP32 arithmetic
-  KIND_FOURSTEP_L2 = 6  // both four-step phases in one persistent launch (N = L * L)
+  KIND_FOURSTEP_L2 = 6, // both four-step phases in one persistent launch (N = L * L)
+  KIND_TMEM2 = 7        // N = 2 H on one SM, one half in tensor memory (tmem2.cuh)
 };
 
 struct KernelEntry {

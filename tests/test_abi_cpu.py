@@ -6,6 +6,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 import paper_2603_27569_gb300 as fg
@@ -118,12 +119,20 @@ def test_configs_listed_for_every_supported_size(L):
                 assert prod == N // c["n1"] and N % c["n1"] == 0
     assert fg.fft_list_configs(12) == []
     assert fg.fft_list_configs(1 << 21) == []
-    for e in range(15, 21):   # beyond one CTA: four-step, and clusters up to 2^16
+    for e in range(15, 21):   # beyond one CTA: four-step, clusters up to 2^16, halves at 2^15
         N = 1 << e
         cfgs = fg.fft_list_configs(N)
         four = [c for c in cfgs if c["path"] == fg.FFT_PATH_FOURSTEP]
         split = [c for c in cfgs if c["path"] == fg.FFT_PATH_SINGLE_CTA]
-        assert four and len(four) + len(split) == len(cfgs)
+        halves = [c for c in cfgs if c["path"] == fg.FFT_PATH_TMEM_HALVES]
+        assert four and len(four) + len(split) + len(halves) == len(cfgs)
+        # one SM per row, half of it in tensor memory: each half is one
+        # 16384-point Stockham schedule of 512 threads x 32 points
+        assert bool(halves) == (N == 1 << 15)
+        for c in halves:
+            assert int(np.prod(c["radix"][:c["num_passes"]])) * 2 == N
+            assert c["threads_per_cta"] * c["points_per_thread"] * 2 == N
+            assert c["points_per_thread"] == 32 and not c["cluster_split"]
         assert all(c["cluster_split"] in (2, 4, 8) for c in split)
         assert bool(split) == (N <= 1 << 16)
         for c in split:

@@ -303,13 +303,18 @@ def test_host_buffer_exec_matches_device_exec(N, flags):
 @pytest.mark.parametrize("direction", [fg.FFT_FORWARD, fg.FFT_INVERSE])
 def test_beyond_one_cta(N, direction):
     # N > 16384: the two-phase four-step (phase 1 <= 256 points, phase 2 <=
-    # 4096), also forced; every listed configuration (four-step splits and
-    # cluster rows), ragged CTA tail included
+    # 4096), also forced; every listed configuration (four-step splits,
+    # cluster rows, halves in tensor memory), ragged CTA tail included.  The
+    # default is the one-pass kernel with half of each row in tensor memory
+    # at 32768, the four-step above.
     cfgs = fg.fft_list_configs(N)
     assert cfgs
     x = synth.gaussian((3, N), seed=N)
     y, info = run(x, direction)
-    assert info["path"] == fg.FFT_PATH_FOURSTEP and info["n1"] * info["n2"] == N
+    if N == 1 << 15:
+        assert info["path"] == fg.FFT_PATH_TMEM_HALVES and info["n1"] == 0
+    else:
+        assert info["path"] == fg.FFT_PATH_FOURSTEP and info["n1"] * info["n2"] == N
     check(x, y, direction)
     y, info = run(x, direction, flags=fg.FFT_FLAG_FORCE_FOURSTEP)
     assert info["path"] == fg.FFT_PATH_FOURSTEP and info["n1"] * info["n2"] == N
