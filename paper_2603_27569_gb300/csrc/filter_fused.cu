@@ -137,26 +137,56 @@ filter_kernel(FilterArgs a) {
 // Launched as a resident grid (occupancy x SMs) that walks the rows; warp 0
 // asks the bulk-copy engine to prefetch the CTA's next row into L2 when a
 // row starts.
+// Output index of register m after a transform whose last pass is paired (PL:
+// registers 2j, 2j + 1 hold adjacent outputs, moved as one 16-byte access) or
+// not.
+template <int N, int P, class SC, bool PL>
+__device__ __forceinline__ int out_index(int lt, int m) {
+  if constexpr (PL) return final_index_pair<N, P, SC>(lt, m >> 1) + (m & 1);
+  else return final_index<N, P, SC>(lt, m);
+}
+__device__ __forceinline__ float4 pack2(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+
 template <int N, int P, class SC>
 __device__ __noinline__ void filter_half_fwd(const float2 *src, float2 *xs, const float2 *H,
                                              float2 *buf, const float2 *tw, int lt, int active,
                                              int conj_h) {
   constexpr int T = N / P;
+  constexpr bool PL = pairable<N, P, SC>();
   float2 v[P];
 #pragma unroll
   for (int m = 0; m < P; ++m) v[m] = active ? __ldcs(src + lt + m * T) : make_float2(0.f, 0.f);
-  run_passes<N, P, -1, SC, 0, SwizzledRow, 1>(v, lt, buf, tw, SwizzledRow{});
-  // v[m] = (F x)[final_index(lt, m)]
+  run_passes<N, P, -1, SC, 0, SwizzledRow, 1, CtaBarrier, PL>(v, lt, buf, tw, SwizzledRow{});
+  // v[m] = (F x)[out_index(lt, m)]
+  if constexpr (PL) {
 #pragma unroll
-  for (int m = 0; m < P; ++m) {
-    const int k = final_index<N, P, SC>(lt, m);
-    if (active && xs) __stcs(xs + k, v[m]);
-    const float2 h = __ldg(H + k);
-    v[m] = conj_h ? cmulc(v[m], h) : cmul(v[m], h);
+    for (int m = 0; m < P; m += 2) {
+      const int k = out_index<N, P, SC, PL>(lt, m);
+      if (active && xs) __stcs(reinterpret_cast<float4 *>(xs + k), pack2(v[m], v[m + 1]));
+      const float4 h = __ldg(reinterpret_cast<const float4 *>(H + k));
+      v[m] = conj_h ? cmulc(v[m], lo2(h)) : cmul(v[m], lo2(h));
+      v[m + 1] = conj_h ? cmulc(v[m + 1], hi2(h)) : cmul(v[m + 1], hi2(h));
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < P; ++m) {
+      const int k = out_index<N, P, SC, PL>(lt, m);
+      if (active && xs) __stcs(xs + k, v[m]);
+      const float2 h = __ldg(H + k);
+      v[m] = conj_h ? cmulc(v[m], h) : cmul(v[m], h);
+    }
   }
   __syncthreads();  // every read of the buffer by the transform is done
+  if constexpr (PL) {
 #pragma unroll
-  for (int m = 0; m < P; ++m) buf[final_index<N, P, SC>(lt, m)] = v[m];
+    for (int m = 0; m < P; m += 2)
+      *reinterpret_cast<float4 *>(buf + out_index<N, P, SC, PL>(lt, m)) = pack2(v[m], v[m + 1]);
+  } else {
+#pragma unroll
+    for (int m = 0; m < P; ++m) buf[out_index<N, P, SC, PL>(lt, m)] = v[m];
+  }
 }
 
 template <int N, int P, class SC>
@@ -167,10 +197,18 @@ __device__ __noinline__ void filter_half_inv(float2 *buf, float2 *dst, const flo
 #pragma unroll
   for (int m = 0; m < P; ++m) v[m] = buf[lt + m * T];
   __syncthreads();  // every thread has its inputs: the transform may overwrite the buffer
-  run_passes<N, P, +1, SC, 0, SwizzledRow, 1>(v, lt, buf, tw, SwizzledRow{});
+  constexpr bool PL = pairable<N, P, SC>();
+  run_passes<N, P, +1, SC, 0, SwizzledRow, 1, CtaBarrier, PL>(v, lt, buf, tw, SwizzledRow{});
   if (active) {
+    if constexpr (PL) {
 #pragma unroll
-    for (int m = 0; m < P; ++m) __stcs(dst + final_index<N, P, SC>(lt, m), cscale(v[m], scale));
+      for (int m = 0; m < P; m += 2)
+        __stcs(reinterpret_cast<float4 *>(dst + out_index<N, P, SC, PL>(lt, m)),
+               pack2(cscale(v[m], scale), cscale(v[m + 1], scale)));
+    } else {
+#pragma unroll
+      for (int m = 0; m < P; ++m) __stcs(dst + out_index<N, P, SC, PL>(lt, m), cscale(v[m], scale));
+    }
   }
 }
 
@@ -228,16 +266,17 @@ __device__ __noinline__ void filter_half_bwd(const float2 *gy, const float2 *xs,
                                              float2 *buf, const float2 *tw, int lt, float inv_n,
                                              uint32_t taddr) {
   constexpr int T = N / P;
+  constexpr bool PL = pairable<N, P, SC>();
   static_assert(P % 8 == 0, "partial sums move 8 points at a time");
   float2 v[P];
 #pragma unroll
   for (int m = 0; m < P; ++m) v[m] = __ldcs(gy + lt + m * T);
   // this thread's saved-spectrum points into L1 while the transform runs
 #pragma unroll
-  for (int m = 0; m < P; ++m)
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(xs + final_index<N, P, SC>(lt, m)));
-  run_passes<N, P, -1, SC, 0, SwizzledRow, 1>(v, lt, buf, tw, SwizzledRow{});
-  // v[m] = (F g_y)[final_index(lt, m)]; g_z = that / N
+  for (int m = 0; m < P; m += (PL ? 2 : 1))
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(xs + out_index<N, P, SC, PL>(lt, m)));
+  run_passes<N, P, -1, SC, 0, SwizzledRow, 1, CtaBarrier, PL>(v, lt, buf, tw, SwizzledRow{});
+  // v[m] = (F g_y)[out_index(lt, m)]; g_z = that / N
 #pragma unroll
   for (int m = 0; m < P; ++m) v[m] = cscale(v[m], inv_n);
   // Chunk c: its sums' tensor-memory read and its X loads are issued
@@ -245,9 +284,23 @@ __device__ __noinline__ void filter_half_bwd(const float2 *gy, const float2 *xs,
   // latencies overlap.
   float r[16];
   float2 x[8];
-  tmem_ld16(taddr, r);
+  // the saved spectrum of registers 8c .. 8c + 7 (adjacent pairs as 16-byte loads)
+  auto load_x = [&](int c) {
+    if constexpr (PL) {
 #pragma unroll
-  for (int q = 0; q < 8; ++q) x[q] = __ldcs(xs + final_index<N, P, SC>(lt, q));
+      for (int q = 0; q < 8; q += 2) {
+        const float4 t =
+            __ldcs(reinterpret_cast<const float4 *>(xs + out_index<N, P, SC, PL>(lt, 8 * c + q)));
+        x[q] = lo2(t);
+        x[q + 1] = hi2(t);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) x[q] = __ldcs(xs + out_index<N, P, SC, PL>(lt, 8 * c + q));
+    }
+  };
+  tmem_ld16(taddr, r);
+  load_x(0);
 #pragma unroll
   for (int c = 0; c < P / 8; ++c) {
     tmem_wait_ld(r);
@@ -260,16 +313,30 @@ __device__ __noinline__ void filter_half_bwd(const float2 *gy, const float2 *xs,
     tmem_st16(taddr + 16 * c, r);
     if (c + 1 < P / 8) {
       tmem_ld16(taddr + 16 * (c + 1), r);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) x[q] = __ldcs(xs + final_index<N, P, SC>(lt, 8 * (c + 1) + q));
+      load_x(c + 1);
     }
   }
   tmem_wait_st();
+  if constexpr (PL) {
 #pragma unroll
-  for (int m = 0; m < P; ++m) v[m] = cmulc(v[m], __ldg(H + final_index<N, P, SC>(lt, m)));
+    for (int m = 0; m < P; m += 2) {
+      const float4 h = __ldg(reinterpret_cast<const float4 *>(H + out_index<N, P, SC, PL>(lt, m)));
+      v[m] = cmulc(v[m], lo2(h));
+      v[m + 1] = cmulc(v[m + 1], hi2(h));
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = cmulc(v[m], __ldg(H + out_index<N, P, SC, PL>(lt, m)));
+  }
   __syncthreads();  // every read of the buffer by the transform is done
+  if constexpr (PL) {
 #pragma unroll
-  for (int m = 0; m < P; ++m) buf[final_index<N, P, SC>(lt, m)] = v[m];
+    for (int m = 0; m < P; m += 2)
+      *reinterpret_cast<float4 *>(buf + out_index<N, P, SC, PL>(lt, m)) = pack2(v[m], v[m + 1]);
+  } else {
+#pragma unroll
+    for (int m = 0; m < P; ++m) buf[out_index<N, P, SC, PL>(lt, m)] = v[m];
+  }
 }
 
 template <int N, int P, class SC>
@@ -327,7 +394,8 @@ filter_bwd2_kernel(FilterBwdArgs a) {
     tmem_wait_ld(r);
 #pragma unroll
     for (int q = 0; q < 8; ++q)
-      dst[final_index<N, P, SC>(lt, 8 * c + q)] = make_float2(r[2 * q], r[2 * q + 1]);
+      dst[out_index<N, P, SC, pairable<N, P, SC>()>(lt, 8 * c + q)] =
+          make_float2(r[2 * q], r[2 * q + 1]);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
