@@ -247,7 +247,6 @@ __global__ void __launch_bounds__(N / 2 / P, 1) tmem2_kernel(Tmem2Args args) {
   };
   const uint32_t tbase = *tslot;
   const uint32_t tD = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * (warp >> 2));
-  const uint32_t tE = tD + REGION;
   float2 a[P];
   long long row = blockIdx.x;
   if (row < args.batch) {
@@ -259,11 +258,6 @@ __global__ void __launch_bounds__(N / 2 / P, 1) tmem2_kernel(Tmem2Args args) {
   for (; row < args.batch; row += gridDim.x, par ^= 1u) {
     const long long next = row + gridDim.x;
     const bool load_next = next < args.batch;
-    // The first row's own loads come from HBM; its prefetch of the next row
-    // waits until they have landed (after the split).
-    const bool first = row == (long long)blockIdx.x;
-    if (!first && load_next && lt < 32)
-      prefetch_l2_warp(args.in + next * N, (long long)N * (long long)sizeof(float2), lt);
 #pragma unroll 1
     for (int h = 0; h < 2; ++h) {
       // Opaque per round: keeps the loop-invariant twiddle and buffer
@@ -279,7 +273,8 @@ __global__ void __launch_bounds__(N / 2 / P, 1) tmem2_kernel(Tmem2Args args) {
         const float2 wt = __ldg(args.tw_n + ltp);  // read per row: nothing stays live
         tmem2_split_chunk<N, P, D, 0>(a, bufp, ltp, tD, wt);
         tmem_wait_st();
-        if (first && load_next && lt < 32)
+        // the next row into L2 once this row's inputs have landed
+        if (load_next && lt < 32)
           prefetch_l2_warp(args.in + next * N, (long long)N * (long long)sizeof(float2), lt);
         __syncthreads();  // the second half is read: the transform may write the buffer
       } else {
@@ -288,7 +283,7 @@ __global__ void __launch_bounds__(N / 2 / P, 1) tmem2_kernel(Tmem2Args args) {
       }
       run_passes_early<H, P, D, SC, 0, TWM, PAIR_LAST>(a, ltp, bufp, twp, NoHook{}, NoTw{});
       if (h == 0) {
-        tmem2_park_chunk<P, 0>(a, tE);
+        tmem2_park_chunk<P, 0>(a, tD + REGION);
         tmem_wait_st();
       } else {
         // every thread is past round 1's last exchange read: the buffer may
@@ -302,9 +297,9 @@ __global__ void __launch_bounds__(N / 2 / P, 1) tmem2_kernel(Tmem2Args args) {
         const float2 *nsrc = args.in + (load_next ? next : row) * N;
         const float s = args.scale;
         if (args.out32)
-          tmem2_store_chunk<N, P, SC, PAIR_LAST, true, 0>(a, ltp, tE, dst, nsrc, load_next, s);
+          tmem2_store_chunk<N, P, SC, PAIR_LAST, true, 0>(a, ltp, tD + REGION, dst, nsrc, load_next, s);
         else
-          tmem2_store_chunk<N, P, SC, PAIR_LAST, false, 0>(a, ltp, tE, dst, nsrc, load_next, s);
+          tmem2_store_chunk<N, P, SC, PAIR_LAST, false, 0>(a, ltp, tD + REGION, dst, nsrc, load_next, s);
       }
     }
     if (!ok) break;
