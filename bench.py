@@ -776,18 +776,22 @@ def bench_columns(fg, torch, dev):
 
 
 def bench_large_n(fg, torch, dev):
-    """N = 2^15..2^20 (beyond one CTA: the two-phase four-step; and 2^15 on
-    2-CTA clusters for comparison), 2^25 points per call, forward."""
+    """N = 2^15..2^20 beyond one CTA, 2^25 points per call, forward: the
+    default plan (2^15: one pass with half of each row in tensor memory;
+    above: the two-phase four-step), and 2^15 through the four-step and on
+    2-CTA clusters for comparison."""
     out = {}
     x = torch.randn(POINTS, dtype=torch.complex64, device=dev)
     y = torch.empty_like(x)
-    for key in [str(1 << e) for e in range(15, 21)] + ["32768_cluster2"]:
+    for key in [str(1 << e) for e in range(15, 21)] + ["32768_fourstep", "32768_cluster2"]:
         N = int(key.split("_")[0])
-        cfg = None
+        cfg, flags = None, 0
         if key.endswith("cluster2"):
             cfg = next(c for c in fg.fft_list_configs(N)
                        if c["cluster_split"] == 2 and c["twiddle_mode"] == 1)
-        p = fg.Plan(N, POINTS // N, fg.FFT_FORWARD, device=dev, config=cfg)
+        if key.endswith("fourstep"):
+            flags = fg.FFT_FLAG_FORCE_FOURSTEP
+        p = fg.Plan(N, POINTS // N, fg.FFT_FORWARD, device=dev, config=cfg, flags=flags)
         for _ in range(3):
             p(x, out=y)
         torch.cuda.synchronize()
@@ -801,7 +805,8 @@ def bench_large_n(fg, torch, dev):
         ms = a.elapsed_time(b) / reps
         info = p.info()
         p.close()
-        out[key] = {"us": round(ms * 1e3, 2), "n1": info["n1"], "n2": info["n2"],
+        out[key] = {"us": round(ms * 1e3, 2), "path": info["path"], "n1": info["n1"],
+                    "n2": info["n2"],
                     "cluster_split": info["cluster_split"],
                     "gflops": round(flops(N, POINTS // N) / (ms * 1e-3) / 1e9, 1),
                     "frac_hbm": round(16.0 * POINTS / (ms * 1e-3) / 1e9 / peaks()[0], 4)}

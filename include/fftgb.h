@@ -154,11 +154,15 @@ const char *fft_status_string(fft_status_t status);
 
 /*
  * fft_plan — plan `batch` transforms of length N in one direction.
- * N: power of two, 2 <= N <= 2^20.  Up to 16384 a row fits one CTA; above
- * that the two-phase four-step runs (N = n1 * n2 with a phase-1 length
- * n2 <= 256 and a phase-2 length n1 <= 4096; its intermediate doubles the
- * HBM traffic).  Rows on thread-block clusters (cluster_split in
- * fft_config_t, N = 8192 .. 65536) are selectable through fft_plan_config.
+ * N: power of two, 2 <= N <= 2^20.  Up to 16384 a row fits one CTA.  At
+ * 32768 a row still crosses HBM once (path FFT_PATH_TMEM_HALVES: a radix-2
+ * decimation-in-frequency split into two 16384-point halves on one SM, one
+ * half held in tensor memory while the other transforms; one persistent
+ * 512-thread CTA per SM).  Above that the two-phase four-step runs
+ * (N = n1 * n2 with a phase-1 length n2 <= 256 and a phase-2 length
+ * n1 <= 4096; its intermediate doubles the HBM traffic).  Rows on
+ * thread-block clusters (cluster_split in fft_config_t, N = 8192 .. 65536)
+ * and the four-step at 32768 are selectable through fft_plan_config.
  * batch >= 0 (0 makes a valid plan whose
  * exec does nothing).  direction: FFT_FORWARD or FFT_INVERSE.
  * Allocates and fills the plan's twiddle tables on the current device
@@ -186,8 +190,9 @@ fft_status_t fft_plan_ex(fft_plan_t *out, int N, int64_t batch, int direction,
  * fft_list_configs — enumerate the FP32 execution configurations compiled
  * into this library for length N: every single-CTA Stockham variant (radix
  * schedule, points per thread, transforms per CTA), every cluster
- * configuration (cluster_split K, N = 8192 .. 65536) and every four-step
- * split.
+ * configuration (cluster_split K, N = 8192 .. 65536), the tensor-memory
+ * halves at 32768 (path FFT_PATH_TMEM_HALVES; radix: the 16384-point
+ * schedule of each half) and every four-step split.
  * Writes min(count, capacity) entries to out (out may be NULL) and returns
  * the total count (0 for an unsupported N).
  * Paper: Sec. IV-C (radix selection) and Sec. V-D (the per-size kernel
