@@ -331,8 +331,8 @@ static fft_status_t launch_tmem2(const KernelEntry *k, int dir, const float2 *in
   a.scale = scale;
   a.status = status;
   a.out32 = ((uintptr_t)out & 31) == 0;
+  if (rows > 0x7fffffffLL) return FFT_ERR_INVALID_SIZE;  // the kernel indexes rows in 32 bits
   const int64_t grid = grid_cap > 0 && grid_cap < rows ? grid_cap : rows;
-  if (grid > 0x7fffffffLL) return FFT_ERR_INVALID_SIZE;
   void *args[] = {&a};
   FFTGB_CUDA(launch_pdl(k->fn[dir > 0 ? 1 : 0], dim3((unsigned)grid), dim3(k->threads), k->smem,
                         st, args));

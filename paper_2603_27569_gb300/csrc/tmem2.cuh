@@ -237,27 +237,31 @@ __global__ void __launch_bounds__(N / 2 / P, 1) tmem2_kernel(Tmem2Args args) {
   tmem_fence_after();
   // The second half of row r into the exchange buffer (warp 0; the buffer
   // is free: no thread reads it until the copy's barrier completes).
-  auto issue_half = [&](long long r) {
+  auto issue_half = [&](int r) {
     if (warp == 0) {
       if (lt == 0) mbar_expect_tx(bar, kHalf);
       __syncwarp();
       tma_load_1d(reinterpret_cast<char *>(smem) + lt * kPiece,
-                  reinterpret_cast<const char *>(args.in + r * N + H) + lt * kPiece, kPiece, bar);
+                  reinterpret_cast<const char *>(args.in + (long long)r * N + H) + lt * kPiece, kPiece,
+                  bar);
     }
   };
   const uint32_t tbase = *tslot;
   const uint32_t tD = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * (warp >> 2));
   float2 a[P];
-  long long row = blockIdx.x;
-  if (row < args.batch) {
+  // Row indices fit 32 bits: a row is 256 KiB, so 2^31 rows exceed any memory
+  // (the launcher checks batch against INT_MAX).
+  const int batch = (int)args.batch;
+  int row = blockIdx.x;
+  if (row < batch) {
     issue_half(row);
-    load_row<H, P>(a, args.in + row * N, lt);
+    load_row<H, P>(a, args.in + (long long)row * N, lt);
   }
   bool ok = true;
   unsigned par = 0;  // phase of the copy barrier: one completion per row
-  for (; row < args.batch; row += gridDim.x, par ^= 1u) {
-    const long long next = row + gridDim.x;
-    const bool load_next = next < args.batch;
+  for (; row < batch; row += gridDim.x, par ^= 1u) {
+    const int next = row + gridDim.x;
+    const bool load_next = next < batch;
 #pragma unroll 1
     for (int h = 0; h < 2; ++h) {
       // Opaque per round: keeps the loop-invariant twiddle and buffer
@@ -275,7 +279,7 @@ __global__ void __launch_bounds__(N / 2 / P, 1) tmem2_kernel(Tmem2Args args) {
         tmem_wait_st();
         // the next row into L2 once this row's inputs have landed
         if (load_next && lt < 32)
-          prefetch_l2_warp(args.in + next * N, (long long)N * (long long)sizeof(float2), lt);
+          prefetch_l2_warp(args.in + (long long)next * N, (long long)N * (long long)sizeof(float2), lt);
         __syncthreads();  // the second half is read: the transform may write the buffer
       } else {
         tmem2_load_chunk<P, 0>(a, tD);
@@ -293,8 +297,8 @@ __global__ void __launch_bounds__(N / 2 / P, 1) tmem2_kernel(Tmem2Args args) {
           fence_proxy_async();
           issue_half(next);
         }
-        float2 *dst = args.out + row * N;
-        const float2 *nsrc = args.in + (load_next ? next : row) * N;
+        float2 *dst = args.out + (long long)row * N;
+        const float2 *nsrc = args.in + (long long)(load_next ? next : row) * N;
         const float s = args.scale;
         if (args.out32)
           tmem2_store_chunk<N, P, SC, PAIR_LAST, true, 0>(a, ltp, tD + REGION, dst, nsrc, load_next, s);
