@@ -449,6 +449,34 @@ fft_status_t fft_plan_columns(fft_plan_t *out, int L, int64_t ncols, int64_t nma
 fft_status_t fft_fourstep_noalloc(const void *in, void *out, int N, int64_t batch,
                                   int direction, void *stream);
 
+/*
+ * Failure injection, for tests of the library's error paths (no GPU fault,
+ * trap or hang is ever made).  The paper has no counterpart: the paper
+ * reports no error handling; these calls let a test reach the failures that
+ * a healthy GPU never produces.
+ *
+ * fft_debug_fail_alloc — the next `after` device allocations the library
+ * makes succeed and the one after them fails as an out-of-memory cudaMalloc
+ * would (nothing is allocated, no sticky CUDA error is left); the call that
+ * made it returns FFT_ERR_ALLOC and frees what it had allocated.  after < 0
+ * disarms.  Process-wide (all threads and devices); not for production use.
+ */
+void fft_debug_fail_alloc(int after);
+
+/*
+ * fft_debug_bounded_wait — run one of the kernels' bounded device waits on
+ * something that never arrives, with a limit of limit_us microseconds
+ * (1 .. 1000000): kind 0 the mbarrier wait of the bulk-copy kernels (a
+ * barrier expecting one arrival), kind 1 the counter wait of the
+ * single-launch four-step (a counter nobody increments).  The waiting thread
+ * gives up after the limit, records FFT_ERR_TIMEOUT in a device status word
+ * and returns; the call synchronises `stream` and returns that status
+ * (FFT_ERR_TIMEOUT), after which the context stays usable.  Allocates and
+ * frees 8 bytes.  FFT_ERR_INVALID_VALUE for another kind or limit.  The
+ * paper has no counterpart (failure injection, as above).
+ */
+fft_status_t fft_debug_bounded_wait(int kind, int limit_us, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,7 @@ __all__ = [
     "fft_fourstep_noalloc", "FFT_NOALLOC_MAX_POINTS", "fft_plan_columns", "FFT_PATH_COLUMNS",
     "FFT_PATH_TMEM_HALVES",
     "fft_ragged_class_config", "FFT_FLAG_RAGGED_AUTOTUNE", "fft_ragged_list_configs",
-    "fft_ragged_choose",
+    "fft_ragged_choose", "fft_debug_fail_alloc", "fft_debug_bounded_wait",
 ]
 
 FFT_FORWARD = -1
@@ -138,6 +138,8 @@ _SIGS = {
     "fft_plan_config": ([ctypes.POINTER(_vp), _i32, _i64, _i32, _i32, ctypes.POINTER(Config)], _i32),
     "fft_fourstep_noalloc": ([_vp, _vp, _i32, _i64, _i32, _vp], _i32),
     "fft_plan_columns": ([ctypes.POINTER(_vp), _i32, _i64, _i64, _i64, _i64, _i32, _i32], _i32),
+    "fft_debug_fail_alloc": ([_i32], None),
+    "fft_debug_bounded_wait": ([_i32, _i32, _vp], _i32),
 }
 EXPORTED_SYMBOLS = tuple(_SIGS)
 
@@ -352,6 +354,16 @@ def fft_plan_columns(L: int, ncols: int, nmat: int, row_stride: int, mat_stride:
     _check(lib().fft_plan_columns(ctypes.byref(h), L, ncols, nmat, row_stride, mat_stride,
                                   direction, flags), "fft_plan_columns")
     return h.value
+
+
+def fft_debug_fail_alloc(after: int) -> None:
+    """Failure injection: the allocation after the next `after` fails (-1 disarms)."""
+    lib().fft_debug_fail_alloc(int(after))
+
+
+def fft_debug_bounded_wait(kind: int, limit_us: int, stream=None) -> int:
+    """Runs a bounded device wait that nothing satisfies; returns the status code."""
+    return int(lib().fft_debug_bounded_wait(int(kind), int(limit_us), _stream(stream)))
 
 
 def fft_fourstep_noalloc(inp, out, N: int, batch: int, direction: int, stream=None) -> None:

@@ -186,7 +186,7 @@ fft_status_t build_twiddles(fft_plan_impl *pl, const std::vector<TwSeg> &segs) {
   pl->tw_segs = segs;
   pl->tw_count = total;
   if (total == 0) return FFT_OK;
-  if (cudaMalloc(&pl->d_tw, sizeof(float2) * (size_t)total) != cudaSuccess) {
+  if (dev_malloc(&pl->d_tw, sizeof(float2) * (size_t)total) != cudaSuccess) {
     cudaGetLastError();
     return FFT_ERR_ALLOC;
   }
@@ -598,7 +598,7 @@ static fft_status_t plan_fourstep(fft_plan_impl *pl, int want_n1, int l2_rows) {
     const int64_t slots = std::min<int64_t>(pl->l2_slots, nch);
     pl->scratch_bytes = (int64_t)sizeof(float2) * pl->N * l2_rows * slots;
     const int64_t ncnt = 2 + 2 * std::max<int64_t>(nch, 1);
-    if (cudaMalloc(&pl->d_l2cnt, sizeof(unsigned) * (size_t)ncnt) != cudaSuccess) {
+    if (dev_malloc(&pl->d_l2cnt, sizeof(unsigned) * (size_t)ncnt) != cudaSuccess) {
       cudaGetLastError();
       return FFT_ERR_ALLOC;
     }
@@ -608,7 +608,7 @@ static fft_status_t plan_fourstep(fft_plan_impl *pl, int want_n1, int l2_rows) {
     pl->scratch_bytes = (int64_t)sizeof(float2) * pl->N * pl->batch;
   }
   if (pl->scratch_bytes > 0) {
-    if (cudaMalloc(&pl->d_scratch, (size_t)pl->scratch_bytes) != cudaSuccess) {
+    if (dev_malloc(&pl->d_scratch, (size_t)pl->scratch_bytes) != cudaSuccess) {
       cudaGetLastError();
       return FFT_ERR_ALLOC;
     }
@@ -743,7 +743,7 @@ static fft_status_t plan_common(fft_plan_t *out, int N, int64_t batch, int direc
   }
   cudaGetDevice(&pl->device);
   fft_status_t s = FFT_OK;
-  if (cudaMalloc(&pl->d_status, sizeof(int)) != cudaSuccess) {
+  if (dev_malloc(&pl->d_status, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     s = FFT_ERR_ALLOC;
   } else if (cudaMemset(pl->d_status, 0, sizeof(int)) != cudaSuccess) {
@@ -996,7 +996,7 @@ fft_status_t fft_exec_host(fft_plan_t plan, const void *host_in, void *host_out,
   if (!pl->d_stage) {
     int64_t rows = std::max<int64_t>(1, (32ll << 20) / row_bytes);
     rows = std::min(rows, pl->batch);
-    if (cudaMalloc(&pl->d_stage, (size_t)(4 * rows * row_bytes)) != cudaSuccess) {
+    if (dev_malloc(&pl->d_stage, (size_t)(4 * rows * row_bytes)) != cudaSuccess) {
       cudaGetLastError();
       return FFT_ERR_ALLOC;
     }
@@ -1098,7 +1098,7 @@ fft_status_t fft_plan_columns(fft_plan_t *out, int L, int64_t ncols, int64_t nma
   pl->col_mat_stride = mat_stride;
   cudaGetDevice(&pl->device);
   fft_status_t s = FFT_OK;
-  if (cudaMalloc(&pl->d_status, sizeof(int)) != cudaSuccess) {
+  if (dev_malloc(&pl->d_status, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     s = FFT_ERR_ALLOC;
   } else if (cudaMemset(pl->d_status, 0, sizeof(int)) != cudaSuccess) {

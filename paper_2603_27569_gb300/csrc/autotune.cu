@@ -166,7 +166,7 @@ fft_status_t fft_autotune(int N, int direction, int precision, int64_t batch,
   fft_list_configs(N, cfgs.data(), ncfg);
   float2 *in = nullptr, *out = nullptr;
   const size_t bytes = sizeof(float2) * (size_t)N * (size_t)batch;
-  if (cudaMalloc(&in, bytes) != cudaSuccess || cudaMalloc(&out, bytes) != cudaSuccess) {
+  if (dev_malloc(&in, bytes) != cudaSuccess || dev_malloc(&out, bytes) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(in);
     return FFT_ERR_ALLOC;

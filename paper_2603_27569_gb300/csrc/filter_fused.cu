@@ -517,7 +517,7 @@ fft_status_t fft_filter_plan(fft_plan_t *out, int N, int64_t batch) {
     delete h;
     return e;
   };
-  if (cudaMalloc(&pl->d_status, sizeof(int)) != cudaSuccess) {
+  if (dev_malloc(&pl->d_status, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     return fail(FFT_ERR_ALLOC);
   }
@@ -551,7 +551,7 @@ fft_status_t fft_filter_plan(fft_plan_t *out, int N, int64_t batch) {
     f->bwd_grid = (int)std::min<int64_t>((int64_t)occ * sms, batch);
     work = std::max<int64_t>(work, (int64_t)f->bwd_grid * N * (int64_t)sizeof(float2));
   }
-  if (work > 0 && cudaMalloc(&f->d_work, (size_t)work) != cudaSuccess) {
+  if (work > 0 && dev_malloc(&f->d_work, (size_t)work) != cudaSuccess) {
     cudaGetLastError();
     return fail(FFT_ERR_ALLOC);
   }

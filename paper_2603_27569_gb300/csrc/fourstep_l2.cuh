@@ -59,14 +59,16 @@ __device__ __forceinline__ unsigned long long l2_timer_ns() {
   return t;
 }
 
-// Thread 0 waits until *cnt >= target (bounded); returns false on time-out.
-__device__ __forceinline__ bool wait_count(const unsigned *cnt, unsigned target) {
+// Thread 0 waits until *cnt >= target (bounded by limit_ns); returns false on
+// time-out.
+__device__ __forceinline__ bool wait_count(const unsigned *cnt, unsigned target,
+                                           unsigned long long limit_ns = kL2WaitNs) {
   if (ld_acquire(cnt) >= target) return true;
   const unsigned long long t0 = l2_timer_ns();
   while (true) {
     __nanosleep(256);
     if (ld_acquire(cnt) >= target) return true;
-    if (l2_timer_ns() - t0 > kL2WaitNs) return false;
+    if (l2_timer_ns() - t0 > limit_ns) return false;
   }
 }
 

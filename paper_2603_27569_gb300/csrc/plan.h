@@ -74,6 +74,14 @@ struct fft_plan_impl {
   void *filter = nullptr;
 };
 
+// Every device allocation of the library (debug.cu): cudaMalloc, or the
+// failure that fft_debug_fail_alloc armed.
+cudaError_t dev_malloc_raw(void **p, size_t bytes);
+template <class T>
+inline cudaError_t dev_malloc(T **p, size_t bytes) {
+  return dev_malloc_raw(reinterpret_cast<void **>(p), bytes);
+}
+
 // Helpers implemented in api.cu, shared with the other units.
 fft_status_t cuda_status(cudaError_t e);
 // Launch with programmatic stream serialization: the kernel must begin with

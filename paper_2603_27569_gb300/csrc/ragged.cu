@@ -494,7 +494,7 @@ static fft_status_t build_tables(RaggedState *r) {
       p *= rt.radix[k];
     }
   }
-  if (cudaMalloc(&r->d_tw, sizeof(float2) * std::max<int64_t>(1, total)) != cudaSuccess)
+  if (dev_malloc(&r->d_tw, sizeof(float2) * std::max<int64_t>(1, total)) != cudaSuccess)
     return FFT_ERR_ALLOC;
   int64_t off = 0;
   for (auto &pr : passes) {
@@ -526,11 +526,11 @@ static int tune_class(RaggedState *r, int log2n, int dir, int rows) {
   int best = cands[0];
   float best_ms = 1e30f;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (cudaMalloc(&x, pts * sizeof(float2)) != cudaSuccess ||
-      cudaMalloc(&y, pts * sizeof(float2)) != cudaSuccess ||
-      cudaMalloc(&dd, rows * sizeof(RaggedDesc)) != cudaSuccess ||
-      cudaMalloc(&du, (rows + 1) * sizeof(RaggedUnit)) != cudaSuccess ||
-      cudaMalloc(&cnt, 3 * sizeof(unsigned)) != cudaSuccess ||
+  if (dev_malloc(&x, pts * sizeof(float2)) != cudaSuccess ||
+      dev_malloc(&y, pts * sizeof(float2)) != cudaSuccess ||
+      dev_malloc(&dd, rows * sizeof(RaggedDesc)) != cudaSuccess ||
+      dev_malloc(&du, (rows + 1) * sizeof(RaggedUnit)) != cudaSuccess ||
+      dev_malloc(&cnt, 3 * sizeof(unsigned)) != cudaSuccess ||
       cudaMemset(cnt, 0, 3 * sizeof(unsigned)) != cudaSuccess ||
       cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     goto done;
@@ -633,10 +633,11 @@ extern "C" fft_status_t fft_ragged_plan(fft_plan_t *out, int count, const int *N
   auto fail = [&](fft_status_t e) {
     ragged_free(r);
     pl->ragged = nullptr;
+    if (pl->d_status) cudaFree(pl->d_status);
     delete h;
     return e;
   };
-  if (cudaMalloc(&pl->d_status, sizeof(int)) != cudaSuccess) return fail(FFT_ERR_ALLOC);
+  if (dev_malloc(&pl->d_status, sizeof(int)) != cudaSuccess) return fail(FFT_ERR_ALLOC);
   if (cudaMemset(pl->d_status, 0, sizeof(int)) != cudaSuccess) return fail(FFT_ERR_CUDA);
   if (cudaFuncSetAttribute((const void *)ragged_kernel,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRagSmem) !=
@@ -702,9 +703,9 @@ extern "C" fft_status_t fft_ragged_plan(fft_plan_t *out, int count, const int *N
     r->max_out = std::max<int64_t>(r->max_out, out_offset[idx[i]] + N[idx[i]]);
   }
   const size_t ub = sizeof(RaggedUnit) * std::max<size_t>(1, units.size());
-  if (cudaMalloc(&r->d_desc, sizeof(RaggedDesc) * std::max(1, count)) != cudaSuccess ||
-      cudaMalloc(&r->d_units, ub) != cudaSuccess ||
-      cudaMalloc(&r->d_counter, 3 * sizeof(unsigned)) != cudaSuccess ||
+  if (dev_malloc(&r->d_desc, sizeof(RaggedDesc) * std::max(1, count)) != cudaSuccess ||
+      dev_malloc(&r->d_units, ub) != cudaSuccess ||
+      dev_malloc(&r->d_counter, 3 * sizeof(unsigned)) != cudaSuccess ||
       cudaMemset(r->d_counter, 0, 3 * sizeof(unsigned)) != cudaSuccess)
     return fail(FFT_ERR_ALLOC);
   if (count > 0 &&

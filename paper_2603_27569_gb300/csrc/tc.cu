@@ -548,8 +548,8 @@ fft_status_t tc_plan(fft_plan_impl *pl) {
   }
   fft_status_t s = build_twiddles(pl, segs);
   if (s != FFT_OK) return s;
-  if (cudaMalloc(&st->d_bimg, 2 * 4096) != cudaSuccess ||
-      cudaMalloc(&st->d_twx, sizeof(float2) * (size_t)kTcTwx) != cudaSuccess) {
+  if (dev_malloc(&st->d_bimg, 2 * 4096) != cudaSuccess ||
+      dev_malloc(&st->d_twx, sizeof(float2) * (size_t)kTcTwx) != cudaSuccess) {
     cudaGetLastError();
     return FFT_ERR_ALLOC;
   }
