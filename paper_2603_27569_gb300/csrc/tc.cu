@@ -321,20 +321,27 @@ tc_kernel(TcArgs a) {
 #pragma unroll
     for (int s = 0; s < C::S; ++s) {
       if (tid == 0) {
+        // A descriptor holds the operand's shared-memory address / 16 in its
+        // low 14 bits (addresses < 256 KiB), so the descriptor of base + off
+        // is the base descriptor + off / 16: one 64-bit add per operand, the
+        // offsets compile-time constants (all offsets are multiples of 16).
         const uint32_t idesc = tc_idesc<PREC>();
-        const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bs),
-                       bl = smem_u32(Bs + 2048);
-#pragma unroll 1
+        const uint64_t dA = tc_desc(smem_u32(Ahi), C::LBO, C::SBO);
+        const uint64_t dB = tc_desc(smem_u32(Bs), 128, 512);
+        constexpr uint32_t kLo = (uint32_t)L::PLANE / 16;  // Alo - Ahi
+        static_assert(L::PLANE % 16 == 0 && 16 * C::SBO % 16 == 0, "16-byte operand offsets");
+#pragma unroll
         for (int t = 0; t < TM; ++t) {
           const uint32_t d = tbase + 32 * t;
-          const uint32_t arow = 16 * t * C::SBO;
+          const uint32_t arow = 16 * t * C::SBO / 16;
 #pragma unroll
           for (int pr = 0; pr < 3; ++pr) {
-            const uint32_t A = (pr == 2 ? al : ah) + arow, B = pr == 1 ? bl : bh;
 #pragma unroll
-            for (int kk = 0; kk < 2; ++kk)
-              tc_mma(d, tc_desc(A + kk * 2 * C::LBO, C::LBO, C::SBO),
-                     tc_desc(B + kk * 256, 128, 512), idesc, (pr | kk) ? 1u : 0u);
+            for (int kk = 0; kk < 2; ++kk) {
+              const uint64_t A = dA + (pr == 2 ? kLo : 0u) + arow + kk * 2 * C::LBO / 16;
+              const uint64_t B = dB + (pr == 1 ? 2048u / 16 : 0u) + kk * 256 / 16;
+              tc_mma(d, A, B, idesc, (pr | kk) ? 1u : 0u);
+            }
           }
         }
         asm volatile(
