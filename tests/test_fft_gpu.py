@@ -325,7 +325,7 @@ def test_beyond_one_cta(N, direction):
         check(x[:2], y, direction)
 
 
-@pytest.mark.parametrize("N,batch", [(4096, 3000), (16384, 1000)])
+@pytest.mark.parametrize("N,batch", [(4096, 3000), (16384, 1000), (32768, 400)])
 def test_dependent_calls_back_to_back(N, batch):
     # Kernels launched with programmatic dependent launch may become resident
     # while the previous kernel of the stream runs; each call here reads the

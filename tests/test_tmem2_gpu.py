@@ -86,3 +86,14 @@ def test_in_place_and_unaligned_output():
     assert rel_l2_rows(to_host(out).reshape(batch, N)[rows], ref).max() <= TOL_FP32
     assert fg.fft_last_device_status(plan.handle) == 0
     plan.close()
+
+
+def test_host_buffers():
+    # fft_exec_host: pinned host input and output, the rows streamed through
+    # the device in chunks (each chunk one launch of the one-pass kernel)
+    batch = 40
+    x = synth.gaussian((batch, N), seed=12)
+    plan = fg.Plan(N, batch, fg.FFT_INVERSE)
+    y = plan.exec_host(torch.from_numpy(x).pin_memory()).numpy().reshape(batch, N)
+    plan.close()
+    assert rel_l2_rows(y, want(x, fg.FFT_INVERSE)).max() <= TOL_FP32
