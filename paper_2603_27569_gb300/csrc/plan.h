@@ -60,6 +60,8 @@ struct fft_plan_impl {
   // scratch (four-step intermediate)
   float2 *d_scratch = nullptr;
   int64_t scratch_bytes = 0;
+  // one-tile-per-CTA plain kernels: CTAs resident at once (the look-ahead prefetch)
+  int64_t resident_ctas = 0;
   // device status word (bounded waits report here)
   int *d_status = nullptr;
   // host-buffer exec staging
@@ -101,7 +103,7 @@ const KernelEntry *default_stockham(int N);
 const KernelEntry *default_column(int L, int variant);
 fft_status_t launch_stockham(const KernelEntry *k, int dir, const float2 *in, float2 *out,
                              const float2 *tw, int64_t rows, float scale, int64_t grid_cap,
-                             cudaStream_t st);
+                             int64_t ahead, cudaStream_t st);
 // Persistent grid for kernel k with `per_sm` CTAs per SM (-1: occupancy).
 int64_t persistent_grid(const KernelEntry *k, int per_sm);
 fft_status_t exec_rows(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t rows,

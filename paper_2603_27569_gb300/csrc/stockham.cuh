@@ -64,6 +64,7 @@ struct StockhamArgs {
   const float2 *tw;     // per-pass twiddle tables of this N
   long long batch;      // rows
   float scale;          // applied at the final store (1 or 1/N)
+  long long ahead;      // one tile per CTA: resident CTAs (occupancy x SMs); 0: none
 };
 
 // The r - 1 twiddles W^{j k}, j = 1 .. r-1, of one butterfly.
@@ -420,6 +421,15 @@ stockham_kernel(StockhamArgs args) {
   float2 *buf = smem + b * N;
   const long long ntiles = (args.batch + TB - 1) / TB;
   long long tile = blockIdx.x;
+  // One tile per CTA: first have the tile of the CTA one resident wave later
+  // prefetched into L2, so that CTA reads its rows from L2 instead of HBM.
+  if (args.ahead > 0 && gridDim.x >= ntiles && threadIdx.x < 32) {
+    const long long t2 = tile + args.ahead;
+    if (t2 < ntiles) {
+      const long long rows = args.batch - t2 * TB < TB ? args.batch - t2 * TB : TB;
+      prefetch_l2_warp(args.in + t2 * TB * N, rows * N * (long long)sizeof(float2), threadIdx.x);
+    }
+  }
   float2 a[P];
   // Rows past the batch exist only in the last tile (all later tiles of
   // this CTA would be past it too), so an inactive row ends the loop.
