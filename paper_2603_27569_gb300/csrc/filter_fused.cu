@@ -47,6 +47,7 @@ struct FilterArgs {
   long long batch;
   int conj_h;             // multiply by conj(H) instead of H
   float scale;            // applied at the final store
+  long long ahead;        // one tile per CTA: resident CTAs (the look-ahead prefetch)
 };
 
 // Register budget: up to 128 per thread (two CTAs per SM for the 256-thread
@@ -224,8 +225,10 @@ filter_fwd2_kernel(FilterArgs a) {
   float2 *buf = smem + b * N;
   const long long ntiles = (a.batch + TB - 1) / TB;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long next = tile + gridDim.x;
-    if (threadIdx.x < 32 && next < ntiles) {  // the next tile's rows into L2
+    // a resident grid prefetches the CTA's own next tile; a grid of one CTA
+    // per tile, the tile of the CTA one resident wave later
+    const long long next = tile + (gridDim.x >= ntiles ? a.ahead : gridDim.x);
+    if (threadIdx.x < 32 && next > tile && next < ntiles) {  // that tile's rows into L2
       const long long rows = a.batch - next * TB < TB ? a.batch - next * TB : TB;
       prefetch_l2_warp(a.in + next * TB * N, rows * N * (long long)sizeof(float2), threadIdx.x);
     }
@@ -600,10 +603,9 @@ fft_status_t fft_filter_forward(fft_plan_t plan, const void *x, const void *H, v
       if (p < q + bytes && q < p + bytes) return FFT_ERR_INVALID_VALUE;
     }
   }
-  if (f->v.fwd.fn && f->fwd_grid > 0) {  // persistent: a resident grid walks the rows
-    void *args[] = {&a};
-    return cuda_status(launch_pdl(f->v.fwd.fn, dim3((unsigned)f->fwd_grid), dim3(f->v.fwd.threads),
-                                  f->v.fwd.smem, st, args));
+  if (f->v.fwd.fn && f->fwd_grid > 0) {  // one CTA per row, prefetching a resident wave ahead
+    a.ahead = f->fwd_grid;
+    return filter_launch(f->v.fwd, a, st);
   }
   if (f->v.fwd.fn) return filter_launch(f->v.fwd, a, st);
   // two kernels: F x into X_save (or y), then y = G (F x * H) from there
