@@ -477,6 +477,24 @@ void fft_debug_fail_alloc(int after);
  */
 fft_status_t fft_debug_bounded_wait(int kind, int limit_us, void *stream);
 
+/*
+ * Bounds-checking debug build (the library compiled with FFTGB_BOUNDS_CHECK,
+ * e.g. build.build(debug=True)); the product build has no checks.  In the
+ * single-CTA Stockham kernels every global load and store (row in the batch,
+ * index in the row), pass-table read and exchange-buffer access checks its
+ * index; a check that fails records a site number and skips its access, so a
+ * wrong index is reported, never faulted on.  The paper has no counterpart
+ * (it is the library's substitute for a memory checker).
+ * fft_debug_bounds_status — synchronises the device and returns the first
+ * failed site since the last call (0: none; the record is cleared), -1 in
+ * the product build, -2 on a CUDA error.
+ * fft_debug_bounds_selftest — fails one check on purpose (site 99; nothing
+ * is accessed) on `stream` and synchronises; FFT_ERR_NOT_SUPPORTED in the
+ * product build.  The paper has no counterpart.
+ */
+int fft_debug_bounds_status(void);
+fft_status_t fft_debug_bounds_selftest(void *stream);
+
 #ifdef __cplusplus
 }
 #endif

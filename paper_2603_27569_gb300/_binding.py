@@ -28,6 +28,7 @@ __all__ = [
     "FFT_PATH_TMEM_HALVES",
     "fft_ragged_class_config", "FFT_FLAG_RAGGED_AUTOTUNE", "fft_ragged_list_configs",
     "fft_ragged_choose", "fft_debug_fail_alloc", "fft_debug_bounded_wait",
+    "fft_debug_bounds_status", "fft_debug_bounds_selftest",
 ]
 
 FFT_FORWARD = -1
@@ -52,7 +53,9 @@ STATUS = {
 }
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "_build", "libfftgb.so")
+# The product library, or the bounds-checking debug build when FFTGB_LIBRARY
+# names it (build.build(debug=True) returns its path).
+_LIB_PATH = os.environ.get("FFTGB_LIBRARY") or os.path.join(_HERE, "_build", "libfftgb.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -140,6 +143,8 @@ _SIGS = {
     "fft_plan_columns": ([ctypes.POINTER(_vp), _i32, _i64, _i64, _i64, _i64, _i32, _i32], _i32),
     "fft_debug_fail_alloc": ([_i32], None),
     "fft_debug_bounded_wait": ([_i32, _i32, _vp], _i32),
+    "fft_debug_bounds_status": ([], _i32),
+    "fft_debug_bounds_selftest": ([_vp], _i32),
 }
 EXPORTED_SYMBOLS = tuple(_SIGS)
 
@@ -364,6 +369,17 @@ def fft_debug_fail_alloc(after: int) -> None:
 def fft_debug_bounded_wait(kind: int, limit_us: int, stream=None) -> int:
     """Runs a bounded device wait that nothing satisfies; returns the status code."""
     return int(lib().fft_debug_bounded_wait(int(kind), int(limit_us), _stream(stream)))
+
+
+def fft_debug_bounds_status() -> int:
+    """Debug build: first failed bounds-check site since the last call (0: none,
+    cleared on read); -1 in the product build (no checks compiled)."""
+    return int(lib().fft_debug_bounds_status())
+
+
+def fft_debug_bounds_selftest(stream=None) -> int:
+    """Debug build: fails one bounds check on purpose (nothing is accessed)."""
+    return int(lib().fft_debug_bounds_selftest(_stream(stream)))
 
 
 def fft_fourstep_noalloc(inp, out, N: int, batch: int, direction: int, stream=None) -> None:

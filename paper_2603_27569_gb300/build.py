@@ -37,8 +37,8 @@ def _newest_header() -> float:
     return max((os.path.getmtime(h) for h in hs), default=0.0)
 
 
-def _compile(src: str, obj: str, verbose: bool) -> str:
-    cmd = [_nvcc()] + NVCC_FLAGS + ["-c", src, "-o", obj]
+def _compile(src: str, obj: str, verbose: bool, extra=()) -> str:
+    cmd = [_nvcc()] + NVCC_FLAGS + list(extra) + ["-c", src, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -47,33 +47,41 @@ def _compile(src: str, obj: str, verbose: bool) -> str:
     return r.stderr
 
 
-def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None,
+          debug: bool = False) -> str:
+    """Compile every csrc/*.cu and link the library.  debug=True builds the
+    bounds-checking variant (FFTGB_BOUNDS_CHECK: every checked index that is
+    out of range is recorded and its access skipped) into _build_debug/; load
+    it by setting FFTGB_LIBRARY to the returned path before the first call."""
+    out = OUT + "_debug" if debug else OUT
+    lib = os.path.join(out, "libfftgb.so")
+    extra = ["-DFFTGB_BOUNDS_CHECK"] if debug else []
+    os.makedirs(out, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdr = _newest_header()
     todo = []
     objs = []
     for s in srcs:
-        o = os.path.join(OUT, os.path.basename(s)[:-3] + ".o")
+        o = os.path.join(out, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), hdr):
             todo.append((s, o))
     jobs = jobs or min(len(todo) or 1, os.cpu_count() or 4)
     if todo:
         with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
-            futs = {ex.submit(_compile, s, o, verbose): s for s, o in todo}
+            futs = {ex.submit(_compile, s, o, verbose, extra): s for s, o in todo}
             for f in cf.as_completed(futs):
                 log = f.result()
                 if verbose and log:
                     sys.stderr.write(log)
-    if todo or not os.path.exists(LIB):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if todo or not os.path.exists(lib):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [_nvcc(), "-shared"] + ARCH + ["-o", tmp] + objs + ["-cudart", "static"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

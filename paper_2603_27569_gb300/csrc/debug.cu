@@ -11,10 +11,16 @@
 //   thread gives up, records FFT_ERR_TIMEOUT in a device status word and
 //   returns, and the host reads that word: the error path of a lost bulk copy
 //   or a stalled producer, exercised without one.
+//
+//   Debug build (FFTGB_BOUNDS_CHECK, check.cuh): fft_debug_bounds_status()
+//   reports the first failed bounds check of any unit (0: none) and clears
+//   them; fft_debug_bounds_selftest() fails one check on purpose (the access
+//   it guards is skipped) to show the checks are live.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <atomic>
+#include <vector>
 
 #include "fourstep_l2.cuh"
 #include "plan.h"
@@ -55,11 +61,52 @@ __global__ void debug_wait_kernel(int kind, unsigned long long limit_ns, unsigne
   *status = ok ? 0 : 6 /* FFT_ERR_TIMEOUT */;
 }
 
+#ifdef FFTGB_BOUNDS_CHECK
+// The per-unit error-word readers (check.cuh), registered at load time.
+static std::vector<int (*)()> &bounds_readers() {
+  static std::vector<int (*)()> v;
+  return v;
+}
+void register_bounds_reader(int (*read_and_clear)()) { bounds_readers().push_back(read_and_clear); }
+
+__global__ void debug_bounds_selftest_kernel(int n) {
+  (void)FFTGB_OK(n, n, kSiteSelfTest);  // one past the end: recorded, nothing accessed
+}
+#endif
+
 }  // namespace fftgb
 
 using namespace fftgb;
 
 extern "C" {
+
+int fft_debug_bounds_status(void) {
+#ifdef FFTGB_BOUNDS_CHECK
+  if (cudaDeviceSynchronize() != cudaSuccess) return -2;
+  int first = 0;
+  for (auto read : bounds_readers()) {
+    const int v = read();
+    if (v < 0) return -2;
+    if (v != 0 && first == 0) first = v;
+  }
+  return first;
+#else
+  return -1;
+#endif
+}
+
+fft_status_t fft_debug_bounds_selftest(void *stream) {
+#ifdef FFTGB_BOUNDS_CHECK
+  cudaStream_t st = (cudaStream_t)stream;
+  debug_bounds_selftest_kernel<<<1, 1, 0, st>>>(4);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+    return FFT_ERR_CUDA;
+  return FFT_OK;
+#else
+  (void)stream;
+  return FFT_ERR_NOT_SUPPORTED;
+#endif
+}
 
 void fft_debug_fail_alloc(int after) { g_fail_after.store(after < 0 ? -1 : after); }
 

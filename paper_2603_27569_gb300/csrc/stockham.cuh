@@ -25,6 +25,7 @@
 #include <stdint.h>
 
 #include "butterfly.cuh"
+#include "check.cuh"
 
 namespace fftgb {
 
@@ -74,9 +75,10 @@ struct StockhamArgs {
 //            for as many complex multiplies.
 template <int r, int p, int TWM>
 __device__ __forceinline__ void load_twiddles(float2 (&w)[r], const float2 *__restrict__ tws, int k) {
+  const bool ok = FFTGB_OK(k, p, kSiteTwiddle);  // entry k of each table row
 #pragma unroll
   for (int j = 1; j < r; ++j)
-    if (TWM == 0 || tw_loaded<r>(j)) w[j] = __ldg(tws + (j - 1) * p + k);
+    if (TWM == 0 || tw_loaded<r>(j)) w[j] = ok ? __ldg(tws + (j - 1) * p + k) : make_float2(1.f, 0.f);
   if constexpr (TWM == 1) derive_twiddles<r>(w);
 }
 
@@ -85,10 +87,12 @@ __device__ __forceinline__ void load_twiddles(float2 (&w)[r], const float2 *__re
 template <int r, int p, int TWM>
 __device__ __forceinline__ void load_twiddles_pair(float2 (&w0)[r], float2 (&w1)[r],
                                                    const float2 *__restrict__ tws, int k0) {
+  const bool ok = FFTGB_OK(k0, p, kSiteTwiddle) && FFTGB_OK(k0 + 1, p, kSiteTwiddle);
 #pragma unroll
   for (int j = 1; j < r; ++j)
     if (TWM == 0 || tw_loaded<r>(j)) {
-      const float4 v = __ldg(reinterpret_cast<const float4 *>(tws + (j - 1) * p + k0));
+      const float4 v = ok ? __ldg(reinterpret_cast<const float4 *>(tws + (j - 1) * p + k0))
+                          : make_float4(1.f, 0.f, 1.f, 0.f);
       w0[j] = make_float2(v.x, v.y);
       w1[j] = make_float2(v.z, v.w);
     }
@@ -167,11 +171,13 @@ __device__ __forceinline__ void pass_compute(float2 (&a)[P], int lt, const float
 // element (idx, c) at idx * C + c (column kernel); 16 consecutive columns
 // make every half-warp access conflict-free without a swizzle.
 struct SwizzledRow {
+  static constexpr int width = 1;  // buffer slots per logical index
   template <int p, int r>
   __device__ __forceinline__ int at(int idx) const { return swz<p, r>(idx); }
 };
 template <int C>
 struct Interleaved {
+  static constexpr int width = C;
   int c;
   template <int p, int r>
   __device__ __forceinline__ int at(int idx) const { return idx * C + c; }
@@ -190,7 +196,11 @@ __device__ __forceinline__ void pass_write(const float2 (&a)[P], int lt, float2 
     const int k = i & (p - 1);
     const int base = (i - k) * r + k;
 #pragma unroll
-    for (int j = 0; j < r; ++j) buf[ly.template at<p, r>(base + j * p)] = a[q + j * Q];
+    for (int j = 0; j < r; ++j) {
+      const int at = ly.template at<p, r>(base + j * p);
+      if (FFTGB_OK(base + j * p, N, kSiteXchgWrite) && FFTGB_OK(at, N * LY::width, kSiteXchgWrite))
+        buf[at] = a[q + j * Q];
+    }
   }
 }
 
@@ -208,14 +218,22 @@ __device__ __forceinline__ void pass_read(float2 (&a)[P], int lt, const float2 *
     const int i0 = bfly<T, P / rn, true>(lt, 0);
 #pragma unroll
     for (int j = 0; j < P / 2; ++j) {
-      const float4 v =
-          *reinterpret_cast<const float4 *>(buf + ly.template at<p, r>(i0 + j * (N / rn)));
+      const int at = ly.template at<p, r>(i0 + j * (N / rn));
+      const float4 v = FFTGB_OK(i0 + 1 + j * (N / rn), N, kSiteXchgRead) &&
+                               FFTGB_OK(at + 1, N * LY::width, kSiteXchgRead)
+                           ? *reinterpret_cast<const float4 *>(buf + at)
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
       a[2 * j] = make_float2(v.x, v.y);
       a[2 * j + 1] = make_float2(v.z, v.w);
     }
   } else {
 #pragma unroll
-    for (int m = 0; m < P; ++m) a[m] = buf[ly.template at<p, r>(lt + m * T)];
+    for (int m = 0; m < P; ++m) {
+      const int at = ly.template at<p, r>(lt + m * T);
+      a[m] = FFTGB_OK(lt + m * T, N, kSiteXchgRead) && FFTGB_OK(at, N * LY::width, kSiteXchgRead)
+                 ? buf[at]
+                 : make_float2(0.f, 0.f);
+    }
   }
 }
 
@@ -274,10 +292,12 @@ struct PassTw {
     const float2 *tws = tw + SC::tw_offset(S);
     if constexpr (PAIRED) {
       const int k0 = bfly<T, Q, true>(lt, 0) & (p - 1);
+      const bool ok = FFTGB_OK(k0, p, kSiteTwiddle) && FFTGB_OK(k0 + 1, p, kSiteTwiddle);
 #pragma unroll
       for (int j = 1; j < r; ++j)
         if (TWM == 0 || tw_loaded<r>(j)) {
-          const float4 v = __ldg(reinterpret_cast<const float4 *>(tws + (j - 1) * p + k0));
+          const float4 v = ok ? __ldg(reinterpret_cast<const float4 *>(tws + (j - 1) * p + k0))
+                              : make_float4(1.f, 0.f, 1.f, 0.f);
           w[0][j] = make_float2(v.x, v.y);
           w[1][j] = make_float2(v.z, v.w);
         }
@@ -285,9 +305,11 @@ struct PassTw {
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
         const int k = bfly<T, Q, false>(lt, q) & (p - 1);
+        const bool ok = FFTGB_OK(k, p, kSiteTwiddle);
 #pragma unroll
         for (int j = 1; j < r; ++j)
-          if (TWM == 0 || tw_loaded<r>(j)) w[q][j] = __ldg(tws + (j - 1) * p + k);
+          if (TWM == 0 || tw_loaded<r>(j))
+            w[q][j] = ok ? __ldg(tws + (j - 1) * p + k) : make_float2(1.f, 0.f);
       }
     }
   }
@@ -387,7 +409,8 @@ template <int N, int P>
 __device__ __forceinline__ void load_row(float2 (&a)[P], const float2 *src, int lt) {
   constexpr int T = N / P;
 #pragma unroll
-  for (int m = 0; m < P; ++m) a[m] = __ldcs(src + lt + m * T);
+  for (int m = 0; m < P; ++m)
+    a[m] = FFTGB_OK(lt + m * T, N, kSiteLoadIdx) ? __ldcs(src + lt + m * T) : make_float2(0.f, 0.f);
 }
 
 // Persistent over tiles of TB rows: CTA c handles tiles c, c + G, c + 2G, ...
@@ -433,7 +456,8 @@ stockham_kernel(StockhamArgs args) {
   float2 a[P];
   // Rows past the batch exist only in the last tile (all later tiles of
   // this CTA would be past it too), so an inactive row ends the loop.
-  if (tile < ntiles && tile * TB + b < args.batch) {
+  if (tile < ntiles && tile * TB + b < args.batch &&
+      FFTGB_OK(tile * TB + b, args.batch, kSiteLoadRow)) {
     load_row<N, P>(a, args.in + (tile * TB + b) * N, lt);
   } else {
 #pragma unroll
@@ -471,7 +495,8 @@ stockham_kernel(StockhamArgs args) {
           if (first) prefetch_next();
         },
         NoTw{});
-    if (active) {
+    if (active && FFTGB_OK(row, args.batch, kSiteStoreRow) &&
+        (!load_next || FFTGB_OK(nrow, args.batch, kSiteLoadRow))) {
       float2 *dst = args.out + row * N;
       const float2 *nsrc = args.in + (load_next ? nrow : row) * N;
       const float s = args.scale;
@@ -479,8 +504,9 @@ stockham_kernel(StockhamArgs args) {
 #pragma unroll
         for (int j = 0; j < P / 2; ++j) {
           const float2 u = cscale(a[2 * j], s), v = cscale(a[2 * j + 1], s);
-          __stcs(reinterpret_cast<float4 *>(dst + final_index_pair<N, P, SC>(ltp, j)),
-                 make_float4(u.x, u.y, v.x, v.y));
+          const int k = final_index_pair<N, P, SC>(ltp, j);
+          if (FFTGB_OK(k, N, kSiteStoreIdx) && FFTGB_OK(k + 1, N, kSiteStoreIdx))
+            __stcs(reinterpret_cast<float4 *>(dst + k), make_float4(u.x, u.y, v.x, v.y));
           if (load_next) {
             a[2 * j] = __ldcs(nsrc + lt + (2 * j) * T);
             a[2 * j + 1] = __ldcs(nsrc + lt + (2 * j + 1) * T);
@@ -489,7 +515,8 @@ stockham_kernel(StockhamArgs args) {
       } else {
 #pragma unroll
         for (int m = 0; m < P; ++m) {
-          __stcs(dst + final_index<N, P, SC>(ltp, m), cscale(a[m], s));
+          const int k = final_index<N, P, SC>(ltp, m);
+          if (FFTGB_OK(k, N, kSiteStoreIdx)) __stcs(dst + k, cscale(a[m], s));
           if (load_next) a[m] = __ldcs(nsrc + lt + m * T);
         }
       }
