@@ -135,9 +135,10 @@ filter_kernel(FilterArgs a) {
 // merge and spill (~0.8 KiB per thread); as calls, each half is allocated on
 // its own and only pointers cross.  One HBM read and one write per point
 // (plus the saved spectrum), the arithmetic of FM_SPEC followed by FM_MULINV.
-// Launched as a resident grid (occupancy x SMs) that walks the rows; warp 0
-// asks the bulk-copy engine to prefetch the CTA's next row into L2 when a
-// row starts.
+// Launched with one CTA per row; warp 0 first asks the bulk-copy engine to
+// prefetch into L2 the row of the CTA one resident wave later (blockIdx +
+// occupancy x SMs), so later waves read their rows from L2.  (Launched as a
+// resident grid instead, each CTA prefetches its own next row.)
 // Output index of register m after a transform whose last pass is paired (PL:
 // registers 2j, 2j + 1 hold adjacent outputs, moved as one 16-byte access) or
 // not.
