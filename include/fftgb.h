@@ -406,15 +406,27 @@ fft_status_t fft_filter_backward(fft_plan_t plan, const void *g_y, const void *H
  * buffer pointer, for input and output alike; each of the nmat * ncols
  * columns gets an L-point transform (W_L = e^{-2 pi i / L}, forward
  * unnormalised, inverse scaled by 1/L unless FFT_FLAG_UNNORMALIZED_INVERSE).
- * L: power of two in [16, 4096].  ncols: a multiple of the kernel's column
- * tile (16 for L <= 512, 8 for 1024 and 2048, 4 for 4096), else
- * FFT_ERR_INVALID_SIZE.
+ * L: power of two in [16, 2^21].  ncols: a multiple of the kernel's column
+ * tile (16 for L <= 512 and for L > 4096, 8 for 1024 and 2048, 4 for 4096),
+ * else FFT_ERR_INVALID_SIZE.
  * row_stride >= ncols and < 2^31; mat_stride >= (L - 1) * row_stride + ncols
  * (matrices do not overlap); nmat >= 0 (0: exec does nothing).  Execute with
  * fft_exec(plan, in, out, stream): device pointers, 8-byte aligned, in == out
  * allowed, any other overlap of the two extents is FFT_ERR_INVALID_VALUE;
- * fft_exec_host is FFT_ERR_NOT_SUPPORTED.  Each CTA reads its columns whole
- * before writing them, so the in-place transform is safe.
+ * fft_exec_host is FFT_ERR_NOT_SUPPORTED.  Up to L = 4096 a column is one
+ * tile in one CTA, read whole before it is written, so the in-place
+ * transform is safe.
+ * L > 4096 (a long aperture): the four-step factorisation of paper Sec. IV-B
+ * (Eq. 3) down the column, L = n1 n2 with n2 = min(512, 2^ceil(log2(L)/2)):
+ * one launch of n2-point column FFTs over the n1 interleaved sub-matrices
+ * (rows j, j + n1, ...), each output row k2 times W_L^{j k2}, into a
+ * plan-owned scratch, then one launch of n1-point column FFTs from the
+ * scratch to the output, row k2 + n2 k1.  n1 * max(row_stride, ncols) and
+ * n2 * row_stride must stay below 2^31 (else FFT_ERR_INVALID_SIZE).  The
+ * scratch holds min(nmat, max(1, 2^30 / (8 L ncols))) matrices
+ * (fft_plan_info: scratch_bytes, n1, n2); more matrices run as several such
+ * pairs of launches.  in == out stays allowed (the input is read whole before
+ * the output is written); executions of one plan may not overlap in time.
  * Paper: Sec. II-D (azimuth compression as batched 1-D FFTs over the other
  * matrix dimension) and Sec. IX-A (the corner turn).
  */

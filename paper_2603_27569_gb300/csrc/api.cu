@@ -102,6 +102,12 @@ const KernelEntry *default_stockham(int N) {
   return any;
 }
 
+// Column transforms: the longest length (n1 = 4096 rows after a 512-point
+// phase 1) and the scratch one pass of a long-column plan may hold (at least
+// one matrix).
+constexpr int kMaxColumnLength = 1 << 21;
+constexpr int64_t kColumnScratchBytes = 1ll << 30;
+
 const KernelEntry *default_column(int L, int variant) {
   for (const auto &e : kernel_registry())
     if (e.kind == KIND_COLUMN && e.N == L && e.variant == variant && e.is_default) return &e;
@@ -661,6 +667,55 @@ static fft_status_t plan_single(fft_plan_impl *pl, const KernelEntry *k, int cta
   return build_twiddles(pl, segs);
 }
 
+// Columns longer than 4096 (L = n1 n2, column.cuh): per chunk of matrices,
+// phase 1 (n2-point columns of the n1 sub-matrices, twiddled) into the
+// compact scratch [row n1 + n1_count k2][col], then phase 2 (n1-point columns
+// of the n2 sub-matrices) into the caller's layout at rows k2 + n2 k1.
+static fft_status_t exec_long_columns(fft_plan_impl *pl, const float2 *in, float2 *out,
+                                      cudaStream_t st) {
+  const int64_t L = pl->N, n1 = pl->n1, n2 = pl->n2, nc = pl->col_ncols;
+  const int64_t rs = pl->col_row_stride, ms = pl->col_mat_stride;
+  for (int64_t m0 = 0; m0 < pl->col_nmat; m0 += pl->col_chunk) {
+    const int64_t nm = std::min(pl->col_chunk, pl->col_nmat - m0);
+    ColumnArgs c1{};
+    c1.in = in + m0 * ms;
+    c1.out = pl->d_scratch;
+    c1.tw = pl->d_tw + pl->tw_col1;
+    c1.tw_a = pl->d_tw + pl->tw_big;
+    c1.nmat = nm * n1;
+    c1.nsub = (int)n1;
+    c1.in_mat_stride = ms;
+    c1.in_sub_stride = rs;
+    c1.in_row_stride = (int)(n1 * rs);
+    c1.out_mat_stride = L * nc;
+    c1.out_sub_stride = nc;
+    c1.out_row_stride = (int)(n1 * nc);
+    c1.ncols = (int)nc;
+    c1.ntot = (int)L;
+    c1.scale = 1.0f;
+    fft_status_t s = launch_column(pl->k_col1, pl->direction, c1, st);
+    if (s != FFT_OK) return s;
+    ColumnArgs c2{};
+    c2.in = pl->d_scratch;
+    c2.out = out + m0 * ms;
+    c2.tw = pl->d_tw + pl->tw_col2;
+    c2.nmat = nm * n2;
+    c2.nsub = (int)n2;
+    c2.in_mat_stride = L * nc;
+    c2.in_sub_stride = n1 * nc;
+    c2.in_row_stride = (int)nc;
+    c2.out_mat_stride = ms;
+    c2.out_sub_stride = rs;
+    c2.out_row_stride = (int)(n2 * rs);
+    c2.ncols = (int)nc;
+    c2.ntot = (int)L;
+    c2.scale = pl->scale;
+    s = launch_column(pl->k_col2, pl->direction, c2, st);
+    if (s != FFT_OK) return s;
+  }
+  return FFT_OK;
+}
+
 static void free_plan(fft_plan_impl *pl) {
   if (!pl) return;
   if (pl->ragged) ragged_destroy(pl);
@@ -969,6 +1024,8 @@ fft_status_t fft_exec(fft_plan_t plan, const void *in, void *out, void *stream) 
       const char *a = (const char *)in, *b = (const char *)out;
       if (a < b + extent && b < a + extent) return FFT_ERR_INVALID_VALUE;
     }
+    if (pl->k_col1) return exec_long_columns(pl, (const float2 *)in, (float2 *)out,
+                                             (cudaStream_t)stream);
     ColumnArgs c{};
     c.in = (const float2 *)in;
     c.out = (float2 *)out;
@@ -1076,17 +1133,39 @@ fft_status_t fft_plan_columns(fft_plan_t *out, int L, int64_t ncols, int64_t nma
                               int flags) {
   if (!out) return FFT_ERR_INVALID_VALUE;
   *out = nullptr;
-  if (!is_pow2(L) || L < 16 || L > 4096) return FFT_ERR_INVALID_SIZE;
+  if (!is_pow2(L) || L < 16 || L > kMaxColumnLength) return FFT_ERR_INVALID_SIZE;
   if (direction != FFT_FORWARD && direction != FFT_INVERSE) return FFT_ERR_INVALID_VALUE;
   if (flags & ~FFT_FLAG_UNNORMALIZED_INVERSE) return FFT_ERR_INVALID_VALUE;
-  const KernelEntry *k = default_column(L, 0);
-  if (!k) return FFT_ERR_NOT_SUPPORTED;
+  // L > 4096: L = n1 n2, phase 1 of length n2 = min(512, 2^ceil(log2 L / 2)),
+  // phase 2 of length n1 <= 4096.
+  int n1 = L, n2 = 1;
+  if (L > 4096) {
+    int lg = 0;
+    while ((1 << lg) < L) ++lg;
+    n2 = std::min(512, 1 << ((lg + 1) / 2));
+    n1 = L / n2;
+  }
+  const KernelEntry *k = default_column(n1, 0);
+  const KernelEntry *k1 = n2 > 1 ? default_column(n2, 2) : nullptr;
+  if (!k || (n2 > 1 && !k1)) return FFT_ERR_NOT_SUPPORTED;
+  const int tile = k1 ? std::max(k->TB, k1->TB) : k->TB;
   if (ncols < 0 || nmat < 0) return FFT_ERR_INVALID_SIZE;
-  if (ncols % k->TB != 0 || ncols > 0x7fffffffLL) return FFT_ERR_INVALID_SIZE;
+  if (ncols % tile != 0 || ncols > 0x7fffffffLL) return FFT_ERR_INVALID_SIZE;
   if (row_stride < ncols || row_stride > 0x7fffffffLL) return FFT_ERR_INVALID_VALUE;
   if (nmat > 1 && mat_stride < (int64_t)(L - 1) * row_stride + ncols) return FFT_ERR_INVALID_VALUE;
   if (mat_stride < 0) return FFT_ERR_INVALID_VALUE;
   if (nmat * (ncols / k->TB) > 0x7fffffffLL) return FFT_ERR_INVALID_SIZE;
+  // The long path's row strides (n1 or n2 rows apart) and grids stay 32-bit.
+  int64_t chunk = 0;
+  if (k1) {
+    if ((int64_t)n1 * std::max(row_stride, ncols) > 0x7fffffffLL ||
+        (int64_t)n2 * row_stride > 0x7fffffffLL)
+      return FFT_ERR_INVALID_SIZE;
+    if (nmat * n1 * (ncols / k1->TB) > 0x7fffffffLL || nmat * n2 * (ncols / k->TB) > 0x7fffffffLL)
+      return FFT_ERR_INVALID_SIZE;
+    const int64_t mat_bytes = (int64_t)sizeof(float2) * L * ncols;
+    chunk = std::max<int64_t>(1, std::min<int64_t>(nmat, kColumnScratchBytes / std::max<int64_t>(1, mat_bytes)));
+  }
   fft_plan_s *h = new (std::nothrow) fft_plan_s;
   if (!h) return FFT_ERR_ALLOC;
   fft_plan_impl *pl = &h->impl;
@@ -1099,10 +1178,14 @@ fft_status_t fft_plan_columns(fft_plan_t *out, int L, int64_t ncols, int64_t nma
                   : 1.0f;
   pl->path = FFT_PATH_COLUMNS;
   pl->k_col2 = k;
+  pl->k_col1 = k1;
+  pl->n1 = k1 ? n1 : 0;
+  pl->n2 = k1 ? n2 : 0;
   pl->col_ncols = ncols;
   pl->col_nmat = nmat;
   pl->col_row_stride = row_stride;
   pl->col_mat_stride = mat_stride;
+  pl->col_chunk = chunk;
   cudaGetDevice(&pl->device);
   fft_status_t s = FFT_OK;
   if (dev_malloc(&pl->d_status, sizeof(int)) != cudaSuccess) {
@@ -1112,10 +1195,35 @@ fft_status_t fft_plan_columns(fft_plan_t *out, int L, int64_t ncols, int64_t nma
     s = FFT_ERR_CUDA;
   }
   if (s == FFT_OK) s = ensure_smem_attr(k);
+  if (s == FFT_OK && k1) s = ensure_smem_attr(k1);
+  if (s == FFT_OK && k1 && chunk > 0 && ncols > 0) {
+    pl->scratch_bytes = (int64_t)sizeof(float2) * L * ncols * chunk;
+    if (dev_malloc(&pl->d_scratch, (size_t)pl->scratch_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      s = FFT_ERR_ALLOC;
+    }
+  }
   if (s == FFT_OK) {
     int64_t off = 0;
     pl->tw_col2 = 0;
-    s = build_twiddles(pl, pass_segments(*k, off));
+    std::vector<TwSeg> segs = pass_segments(*k, off);
+    if (k1) {
+      pl->tw_col1 = off;
+      auto a = pass_segments(*k1, off);
+      segs.insert(segs.end(), a.begin(), a.end());
+      TwSeg g;  // W_L^{j k} at j * n2 + k, j < n1, k < n2
+      g.offset = off;
+      g.kind = 2;
+      g.p = n2;
+      g.r = 0;
+      g.step = 1;
+      g.M = L;
+      g.count = L;
+      pl->tw_big = off;
+      off += g.count;
+      segs.push_back(g);
+    }
+    s = build_twiddles(pl, segs);
   }
   if (s != FFT_OK) {
     free_plan(pl);

@@ -21,6 +21,17 @@
 // the product of two exact table entries from grids laid out [lt][c] and
 // [m][c]: a warp's loads read C consecutive columns (whole sectors) instead
 // of gathering one sector per element from a table of all N powers.
+//
+// Columns longer than one CTA holds (L = L1 L2 > 4096) run the same two
+// phases down the column instead of along a row: input row n = n1 + L1 n2,
+// output row k = k2 + L2 k1.  Phase 1 is an L2-point column FFT of each of the
+// L1 sub-matrices n1 (rows n1, n1 + L1, ...), times W_L^{n1 k2}, the twiddle
+// now indexed by the sub-matrix rather than the column (TWM == 2; a table
+// laid out [n1][k2] of exact powers, one contiguous slice per CTA); phase 2
+// is an L1-point column FFT of each of the L2 sub-matrices k2 of the phase-1
+// result, stored to rows k2 + L2 k1.  A launch therefore covers nmat matrices
+// of nsub sub-matrices each, sub-matrix j of matrix m starting at
+// m * mat_stride + j * sub_stride.
 #pragma once
 #include "stockham.cuh"
 
@@ -30,10 +41,13 @@ struct ColumnArgs {
   const float2 *in;
   float2 *out;
   const float2 *tw;      // per-pass tables of the length-L transform
-  const float2 *tw_a;    // phase 1: W_Ntot^{c lt} at lt * ncols + c, or null
-  const float2 *tw_b;    // phase 1: W_Ntot^{c T m} at m * ncols + c
-  long long nmat;        // number of matrices (batch)
+  const float2 *tw_a;    // TWM 1: W_Ntot^{c lt} at lt * ncols + c; TWM 2:
+                         // W_Ntot^{j k} at j * L + k for sub-matrix j; else null
+  const float2 *tw_b;    // TWM 1: W_Ntot^{c T m} at m * ncols + c
+  long long nmat;        // number of matrices times nsub
   long long in_mat_stride, out_mat_stride;  // elements between matrices
+  long long in_sub_stride, out_sub_stride;  // elements between sub-matrices
+  int nsub;              // sub-matrices per matrix (0 and 1: one)
   int in_row_stride;     // elements between consecutive rows of the input
   int out_row_stride;    // elements between rows of a non-transposed output
   int ncols;             // columns per matrix (multiple of C)
@@ -41,7 +55,9 @@ struct ColumnArgs {
   float scale;
 };
 
-template <int L, int P, int C, int D, class SC, bool TWIDDLE, bool TRANSPOSED>
+// TWM: 0 no twiddle, 1 the row four-step's per-column twiddle (with a
+// transposed store), 2 the per-sub-matrix twiddle of a long column.
+template <int L, int P, int C, int D, class SC, int TWM, bool TRANSPOSED>
 __global__ void __launch_bounds__(C *(L / P))
 column_kernel(ColumnArgs args) {
   static_assert(SC::product() == L, "radix schedule must multiply to L");
@@ -60,17 +76,22 @@ column_kernel(ColumnArgs args) {
   const int c = threadIdx.x % C;
   const int lt = threadIdx.x / C;
   const int tiles_per_mat = args.ncols / C;
-  const long long mat = blockIdx.x / tiles_per_mat;
-  const int c0 = (int)(blockIdx.x - mat * tiles_per_mat) * C;
+  const long long tile_mat = blockIdx.x / tiles_per_mat;
+  const int c0 = (int)(blockIdx.x - tile_mat * tiles_per_mat) * C;
+  long long mat = tile_mat, sub = 0;
+  if (args.nsub > 1) {
+    mat = tile_mat / args.nsub;
+    sub = tile_mat - mat * args.nsub;
+  }
   float2 a[P];
   {
-    const float2 *src = args.in + mat * args.in_mat_stride + c0 + c;
+    const float2 *src = args.in + mat * args.in_mat_stride + sub * args.in_sub_stride + c0 + c;
 #pragma unroll
     for (int m = 0; m < P; ++m) a[m] = __ldg(src + (long long)(lt + m * T) * args.in_row_stride);
   }
   run_passes<L, P, D, SC, 0>(a, lt, smem, args.tw, Interleaved<C>{c});
   // a[m] now holds output index final_index(lt, m) of column c0 + c.
-  if constexpr (TWIDDLE) {
+  if constexpr (TWM == 1) {
     const int col = c0 + c;
     const float2 wa = __ldg(args.tw_a + (long long)lt * args.ncols + col);
 #pragma unroll
@@ -78,6 +99,13 @@ column_kernel(ColumnArgs args) {
       const float2 w = cmul(wa, __ldg(args.tw_b + (long long)m * args.ncols + col));
       a[m] = cmul_dir<D>(a[m], w);
     }
+  } else if constexpr (TWM == 2) {
+    // W_L^{sub k}: the CTA reads one contiguous row of L entries, a warp at
+    // most two adjacent entries per load (all C columns share k).
+    const float2 *tw = args.tw_a + sub * L;
+#pragma unroll
+    for (int m = 0; m < P; ++m)
+      a[m] = cmul_dir<D>(a[m], __ldg(tw + final_index<L, P, SC>(lt, m)));
   }
   if constexpr (TRANSPOSED) {
     // out[col * L + k]: stage through a tile padded to C + 1 columns.
@@ -94,7 +122,7 @@ column_kernel(ColumnArgs args) {
       dst[e] = cscale(smem[k * LD + cl], args.scale);
     }
   } else {
-    float2 *dst = args.out + mat * args.out_mat_stride + c0 + c;
+    float2 *dst = args.out + mat * args.out_mat_stride + sub * args.out_sub_stride + c0 + c;
 #pragma unroll
     for (int m = 0; m < P; ++m)
       dst[(long long)final_index<L, P, SC>(lt, m) * args.out_row_stride] = cscale(a[m], args.scale);

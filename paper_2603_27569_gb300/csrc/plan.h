@@ -44,6 +44,8 @@ struct fft_plan_impl {
   // matrices, element (mat, row, col) at mat * col_mat_stride + row *
   // col_row_stride + col
   int64_t col_ncols = 0, col_nmat = 0, col_row_stride = 0, col_mat_stride = 0;
+  // columns longer than 4096: matrices per pass through the scratch
+  int64_t col_chunk = 0;
   // four-step in one launch with the intermediate in an L2 ring (n1 == n2):
   // chunks of l2_rows rows, l2_slots ring slots, phase 2 of a chunk claimed
   // l2_lag rounds after its phase 1; d_l2cnt = the launch's work counters

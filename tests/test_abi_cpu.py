@@ -163,7 +163,11 @@ def test_column_plan_validates_on_host(L):
     assert L.fft_plan_columns(None, 256, 16, 1, 16, 4096, -1, 0) == INVALID_VALUE
     assert L.fft_plan_columns(ctypes.byref(h), 8, 16, 1, 16, 128, -1, 0) == INVALID_SIZE
     assert h.value is None
-    assert L.fft_plan_columns(ctypes.byref(h), 8192, 16, 1, 16, 1 << 17, -1, 0) == INVALID_SIZE
+    assert L.fft_plan_columns(ctypes.byref(h), 1 << 22, 16, 1, 16, 1 << 26, -1, 0) == INVALID_SIZE
+    assert L.fft_plan_columns(ctypes.byref(h), 3 << 12, 16, 1, 16, 3 << 16, -1, 0) == INVALID_SIZE
+    # L > 4096: 16-column tile, and n1 * row_stride (n1 = 64 at L = 8192) below 2^31
+    assert L.fft_plan_columns(ctypes.byref(h), 8192, 8, 1, 8, 8192 * 8, -1, 0) == INVALID_SIZE
+    assert L.fft_plan_columns(ctypes.byref(h), 8192, 16, 1, 1 << 25, 1 << 38, -1, 0) == INVALID_SIZE
     assert L.fft_plan_columns(ctypes.byref(h), 256, 17, 1, 17, 256 * 17, -1, 0) == INVALID_SIZE
     assert L.fft_plan_columns(ctypes.byref(h), 4096, 6, 1, 6, 4096 * 6, -1, 0) == INVALID_SIZE
     assert L.fft_plan_columns(ctypes.byref(h), 256, 16, 1, 8, 4096, -1, 0) == INVALID_VALUE
