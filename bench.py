@@ -751,14 +751,20 @@ def bench_cufft(torch, dev, per_key_ms, fg):
 def bench_columns(fg, torch, dev):
     """Azimuth pass without a transpose: L-point transforms down the columns
     of one contiguous [L, 2^25 / L] matrix (fft_plan_columns), forward.
-    L > 4096 runs as two launches through the plan's scratch (32 B of HBM
-    traffic per point against the one-pass 16 B that frac_hbm divides by)."""
+    L >= 4096 runs by default as two launches through the plan's scratch (32 B
+    of HBM traffic per point against the one-pass 16 B that frac_hbm divides
+    by); the _twopass and _onelaunch rows force the other route."""
     out = {}
     x = torch.randn(POINTS, dtype=torch.complex64, device=dev)
     y = torch.empty_like(x)
-    for L in (256, 1024, 4096, 16384, 65536):
+    for key in ("256", "1024", "2048", "2048_twopass", "4096", "4096_onelaunch", "16384",
+                "65536"):
+        L = int(key.split("_")[0])
         ncols = POINTS // L
-        p = fg.ColumnPlan(L, ncols, 1, device=dev)
+        flags = {"twopass": fg.FFT_FLAG_FORCE_FOURSTEP,
+                 "onelaunch": fg.FFT_FLAG_FORCE_SINGLE_CTA}.get(key.partition("_")[2], 0)
+        p = fg.ColumnPlan(L, ncols, 1, device=dev, flags=flags)
+        two = p.info()["n2"] > 0
         for _ in range(3):
             p(x, y)
         torch.cuda.synchronize()
@@ -771,7 +777,7 @@ def bench_columns(fg, torch, dev):
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / reps
         p.close()
-        out[str(L)] = {"us": round(ms * 1e3, 2), "ncols": ncols, "launches": 1 if L <= 4096 else 2,
+        out[key] = {"us": round(ms * 1e3, 2), "ncols": ncols, "launches": 2 if two else 1,
                        "gflops": round(flops(L, ncols) / (ms * 1e-3) / 1e9, 1),
                        "frac_hbm": round(16.0 * POINTS / (ms * 1e-3) / 1e9 / peaks()[0], 4)}
     return out

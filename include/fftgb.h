@@ -413,9 +413,12 @@ fft_status_t fft_filter_backward(fft_plan_t plan, const void *g_y, const void *H
  * (matrices do not overlap); nmat >= 0 (0: exec does nothing).  Execute with
  * fft_exec(plan, in, out, stream): device pointers, 8-byte aligned, in == out
  * allowed, any other overlap of the two extents is FFT_ERR_INVALID_VALUE;
- * fft_exec_host is FFT_ERR_NOT_SUPPORTED.  Up to L = 4096 a column is one
+ * fft_exec_host is FFT_ERR_NOT_SUPPORTED.  Up to L = 2048 a column is one
  * tile in one CTA, read whole before it is written, so the in-place
- * transform is safe.
+ * transform is safe.  L = 4096 runs as the two launches below when ncols is a
+ * multiple of 16, else as one launch of 4-column tiles.  flags may add
+ * FFT_FLAG_FORCE_SINGLE_CTA (one launch; L <= 4096) or FFT_FLAG_FORCE_FOURSTEP
+ * (two launches; L >= 2048), else FFT_ERR_NOT_SUPPORTED.
  * L > 4096 (a long aperture): the four-step factorisation of paper Sec. IV-B
  * (Eq. 3) down the column, L = n1 n2 with n2 = min(512, 2^ceil(log2(L)/2)):
  * one launch of n2-point column FFTs over the n1 interleaved sub-matrices

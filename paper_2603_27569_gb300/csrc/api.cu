@@ -495,7 +495,7 @@ constexpr int kDefaultCtasPerSm = 0;
 static int default_ctas_per_sm(int N) { return N >= 16384 ? -1 : kDefaultCtasPerSm; }
 
 // Four-step split N = n1 * n2: n2 (phase 1) a length with a twiddle +
-// transposed-store column kernel (16..256), n1 (phase 2) a length with a
+// transposed-store column kernel (16..512), n1 (phase 2) a length with a
 // plain column kernel (16..4096).
 static bool fourstep_split(int N, int want_n1, int *n1, int *n2) {
   auto ok = [&](int a) {
@@ -508,13 +508,17 @@ static bool fourstep_split(int N, int want_n1, int *n1, int *n2) {
     *n2 = N / want_n1;
     return true;
   }
-  // Prefer n2 >= n1 (longer first-phase transforms), as square as possible;
-  // beyond 256 x 256, phase 1 stays at 256 points and phase 2 grows.
+  // Prefer n2 >= n1 (longer first-phase transforms), as square as possible,
+  // with phase 1 at most 256 points up to N = 2^17 and 512 beyond, where the
+  // 512-point phase 1 costs less than a phase 2 of 2048 or 4096 points
+  // (measured over 2^25 points: 2^17 512 x 256 181 us against 256 x 512
+  // 190 us; 2^20 2048 x 512 256 us against 4096 x 256 277 us).
+  const int cap = N >= (1 << 18) ? 512 : 256;
   int best = 0;
   for (int a = 16; a <= 4096 && a <= N; a *= 2)
-    if (N % a == 0 && ok(a) && a <= N / a) best = a;
+    if (N % a == 0 && ok(a) && a <= N / a && N / a <= cap) best = a;
   for (int a = 16; !best && a <= 4096 && a <= N; a *= 2)
-    if (N % a == 0 && ok(a)) best = a;
+    if (N % a == 0 && ok(a) && N / a <= cap) best = a;
   if (!best) return false;
   *n1 = best;
   *n2 = N / best;
@@ -1135,11 +1139,21 @@ fft_status_t fft_plan_columns(fft_plan_t *out, int L, int64_t ncols, int64_t nma
   *out = nullptr;
   if (!is_pow2(L) || L < 16 || L > kMaxColumnLength) return FFT_ERR_INVALID_SIZE;
   if (direction != FFT_FORWARD && direction != FFT_INVERSE) return FFT_ERR_INVALID_VALUE;
-  if (flags & ~FFT_FLAG_UNNORMALIZED_INVERSE) return FFT_ERR_INVALID_VALUE;
-  // L > 4096: L = n1 n2, phase 1 of length n2 = min(512, 2^ceil(log2 L / 2)),
-  // phase 2 of length n1 <= 4096.
+  const int route = flags & (FFT_FLAG_FORCE_SINGLE_CTA | FFT_FLAG_FORCE_FOURSTEP);
+  if (flags & ~(FFT_FLAG_UNNORMALIZED_INVERSE | route)) return FFT_ERR_INVALID_VALUE;
+  if (route == (FFT_FLAG_FORCE_SINGLE_CTA | FFT_FLAG_FORCE_FOURSTEP)) return FFT_ERR_INVALID_VALUE;
+  if (route == FFT_FLAG_FORCE_SINGLE_CTA && L > 4096) return FFT_ERR_NOT_SUPPORTED;
+  if (route == FFT_FLAG_FORCE_FOURSTEP && L < 2048) return FFT_ERR_NOT_SUPPORTED;
+  // Two launches (L = n1 n2, phase 1 of length n2 = min(512, 2^ceil(log2 L /
+  // 2)), phase 2 of length n1 <= 4096) beyond one CTA's column, on request
+  // from L = 2048, and by default at 4096 when ncols fills 16-column tiles:
+  // the 4-column single-launch tile measured 188 us over 2^25 points against
+  // 165 us for the two 64-point launches (at 2048 one launch stays ahead,
+  // 138 us against 165 us).
+  const bool two = L > 4096 || route == FFT_FLAG_FORCE_FOURSTEP ||
+                   (L == 4096 && route == 0 && ncols > 0 && ncols % 16 == 0);
   int n1 = L, n2 = 1;
-  if (L > 4096) {
+  if (two) {
     int lg = 0;
     while ((1 << lg) < L) ++lg;
     n2 = std::min(512, 1 << ((lg + 1) / 2));

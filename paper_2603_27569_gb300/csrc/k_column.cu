@@ -44,6 +44,7 @@ FFTGB_COLUMN(128, 16, 16, 1, 1, 16, 8);
 FFTGB_COLUMN(256, 16, 16, 0, 1, 16, 16);
 FFTGB_COLUMN(256, 16, 16, 1, 1, 16, 16);
 FFTGB_COLUMN(512, 16, 16, 0, 1, 16, 16, 2);
+FFTGB_COLUMN(512, 16, 16, 1, 1, 16, 16, 2);
 FFTGB_COLUMN(1024, 16, 16, 0, 0, 16, 16, 4);
 FFTGB_COLUMN(1024, 16, 8, 0, 1, 16, 16, 4);
 FFTGB_COLUMN(2048, 16, 8, 0, 1, 16, 16, 8);

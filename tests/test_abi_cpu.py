@@ -16,6 +16,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "fftgb.h")
 
 OK, INVALID_SIZE, INVALID_VALUE, MISALIGNED = 0, 1, 2, 3
+NOT_SUPPORTED = 7
 
 
 def declared_functions():
@@ -142,7 +143,7 @@ def test_configs_listed_for_every_supported_size(L):
             assert prod * c["cluster_split"] == N and prod <= 16384
         for c in four:
             n2 = N // c["n1"]
-            assert c["n1"] * n2 == N and 16 <= n2 <= 256 and c["n1"] <= 4096
+            assert c["n1"] * n2 == N and 16 <= n2 <= 512 and c["n1"] <= 4096
     for N in (8192, 16384):
         assert any(c["path"] == fg.FFT_PATH_FOURSTEP for c in fg.fft_list_configs(N))
 
@@ -173,7 +174,10 @@ def test_column_plan_validates_on_host(L):
     assert L.fft_plan_columns(ctypes.byref(h), 256, 16, 1, 8, 4096, -1, 0) == INVALID_VALUE
     assert L.fft_plan_columns(ctypes.byref(h), 256, 16, 2, 16, 1000, -1, 0) == INVALID_VALUE
     assert L.fft_plan_columns(ctypes.byref(h), 256, 16, 1, 16, 4096, 0, 0) == INVALID_VALUE
-    assert L.fft_plan_columns(ctypes.byref(h), 256, 16, 1, 16, 4096, -1, 0x4) == INVALID_VALUE
+    assert L.fft_plan_columns(ctypes.byref(h), 256, 16, 1, 16, 4096, -1, 0x8) == INVALID_VALUE
+    assert L.fft_plan_columns(ctypes.byref(h), 2048, 16, 1, 16, 2048 * 16, -1, 0x6) == INVALID_VALUE
+    assert L.fft_plan_columns(ctypes.byref(h), 1024, 16, 1, 16, 1024 * 16, -1, 0x4) == NOT_SUPPORTED
+    assert L.fft_plan_columns(ctypes.byref(h), 8192, 16, 1, 16, 8192 * 16, -1, 0x2) == NOT_SUPPORTED
 
 
 def test_every_declaration_cites_its_passage():

@@ -33,6 +33,8 @@ def column_oracle(x: np.ndarray, inverse: bool) -> np.ndarray:
 @pytest.mark.parametrize("L", [16, 256, 1024, 2048, 4096])
 @pytest.mark.parametrize("direction", [fg.FFT_FORWARD, fg.FFT_INVERSE])
 def test_strided_columns_match_oracle(L, direction):
+    # at 4096: 4, 12 and 8 columns take the one-launch 4-column tile (the
+    # two-launch default needs multiples of 16)
     C = TILE[L]
     for nmat, ncols, pad, gap in ((1, C, 0, 0), (2, 3 * C, 16, 40), (3, 2 * C, 5, 0)):
         rs = ncols + pad                       # padded rows
@@ -43,7 +45,7 @@ def test_strided_columns_match_oracle(L, direction):
             buf, shape=(nmat, L, ncols), strides=(ms * e, rs * e, e))
         x = np.array(view)
         plan = fg.ColumnPlan(L, ncols, nmat, rs, ms, direction)
-        assert plan.info()["path"] == fg.FFT_PATH_COLUMNS
+        assert plan.info()["path"] == fg.FFT_PATH_COLUMNS and plan.info()["n2"] == 0
         dev_in = to_dev(buf)
         dev_out = torch.full_like(dev_in, complex(7.0, -7.0))   # canary outside the extent
         plan(dev_in, dev_out)
@@ -210,3 +212,20 @@ def test_long_columns_over_several_scratch_passes():
     torch.cuda.synchronize()
     assert torch.equal(xd.view(torch.float32), yd.view(torch.float32))
     plan.close()
+
+
+@pytest.mark.parametrize("L", [2048, 4096])
+def test_forced_routes_at_2048_and_4096(L):
+    """Both routes of a 2048- or 4096-point column (one CTA per column tile,
+    or the two launches of the long path) match the oracle."""
+    nmat, ncols, pad, gap = 2, 48, 16, 40
+    buf, x, rs, ms = strided_case(L, nmat, ncols, pad, gap, seed=L + 1)
+    for flags, two in ((fg.FFT_FLAG_FORCE_SINGLE_CTA, False), (fg.FFT_FLAG_FORCE_FOURSTEP, True),
+                       (0, L == 4096)):
+        for direction in (fg.FFT_FORWARD, fg.FFT_INVERSE):
+            plan = fg.ColumnPlan(L, ncols, nmat, rs, ms, direction, flags=flags)
+            assert (plan.info()["n2"] > 0) == two
+            _, got = run_strided(plan, buf, nmat, L, ncols, rs, ms)
+            plan.close()
+            err = col_err(got, column_oracle(x, direction > 0))
+            assert err.max() <= TOL_FP32, (flags, direction, err.max())

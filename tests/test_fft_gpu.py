@@ -302,11 +302,12 @@ def test_host_buffer_exec_matches_device_exec(N, flags):
 @pytest.mark.parametrize("N", [1 << e for e in range(15, 21)])
 @pytest.mark.parametrize("direction", [fg.FFT_FORWARD, fg.FFT_INVERSE])
 def test_beyond_one_cta(N, direction):
-    # N > 16384: the two-phase four-step (phase 1 <= 256 points, phase 2 <=
+    # N > 16384: the two-phase four-step (phase 1 <= 512 points, phase 2 <=
     # 4096), also forced; every listed configuration (four-step splits,
     # cluster rows, halves in tensor memory), ragged CTA tail included.  The
     # default is the one-pass kernel with half of each row in tensor memory
-    # at 32768, the four-step above.
+    # at 32768, the four-step above (phase 1 of 256 points up to 2^17, of 512
+    # beyond).
     cfgs = fg.fft_list_configs(N)
     assert cfgs
     x = synth.gaussian((3, N), seed=N)
@@ -315,6 +316,7 @@ def test_beyond_one_cta(N, direction):
         assert info["path"] == fg.FFT_PATH_TMEM_HALVES and info["n1"] == 0
     else:
         assert info["path"] == fg.FFT_PATH_FOURSTEP and info["n1"] * info["n2"] == N
+        assert info["n2"] == (256 if N <= 1 << 17 else 512)
     check(x, y, direction)
     y, info = run(x, direction, flags=fg.FFT_FLAG_FORCE_FOURSTEP)
     assert info["path"] == fg.FFT_PATH_FOURSTEP and info["n1"] * info["n2"] == N
