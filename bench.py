@@ -867,7 +867,8 @@ def bench_fwd_bwd(fg, synth, torch, dev, per_key_ms):
 
 def run_profile_case(args):
     """A small fixed case for ncu: one plan of the sweep's size at N, executed
-    three times (capture the third launch with -s 2 -c 1)."""
+    three times (capture the third launch with -s 2 -c 1; kind columns: one
+    [N, 2^25 / N] matrix, two launches per execution from N = 4096)."""
     import torch
 
     import paper_2603_27569_gb300 as fg
@@ -915,6 +916,12 @@ def run_profile_case(args):
             fg.fft_exec(h, xr, yr, st)
         info = fg.fft_plan_info(h)
         fg.fft_destroy(h)
+    elif kind == "columns":
+        p = fg.ColumnPlan(N, batch, 1, direction=args.profile_direction, flags=args.profile_flags)
+        for _ in range(3):
+            p(x, y)
+        info = p.info()
+        p.close()
     else:
         raise SystemExit(f"unknown --profile-kind {kind}")
     torch.cuda.synchronize()
@@ -945,7 +952,7 @@ def main():
     ap.add_argument("--profile-direction", type=int, default=-1, choices=[-1, 1],
                     help="direction of the profiled plan (kind plan)")
     ap.add_argument("--profile-kind", default="plan",
-                    choices=["plan", "tc", "filter_fwd", "filter_bwd", "ragged"])
+                    choices=["plan", "tc", "filter_fwd", "filter_bwd", "ragged", "columns"])
     ap.add_argument("--profile-config", type=str, default="",
                     help="JSON of one fft_list_configs entry to force")
     args = ap.parse_args()
