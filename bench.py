@@ -852,8 +852,29 @@ def bench_fwd_bwd(fg, synth, torch, dev, per_key_ms):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / reps
 
+    def timed_step():
+        # the whole training step (y, L, grad_x, grad_H) in one persistent kernel
+        # plus the two fixed-order reductions (fft_filter_step)
+        xs, Hs, m32 = x.detach(), layer.H.detach(), m.to(torch.float32).contiguous()
+
+        def once():
+            fg.spectral_filter_step(xs, Hs, m32)
+
+        for _ in range(3):
+            once()
+        torch.cuda.synchronize()
+        reps = 10
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            once()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
     fb_ms = timed(True)
     unfused_ms = timed(False)
+    step_ms = timed_step()
     plain_ms = per_key_ms[(N, fg.FFT_FORWARD)] * rows * N / POINTS
     plain4 = 4 * plain_ms
     return {"workload": "spectral filter y=IFFT(FFT(x)*H), x [4096, 8192] chirp echoes, "
@@ -862,7 +883,10 @@ def bench_fwd_bwd(fg, synth, torch, dev, per_key_ms):
             "fwd_bwd_ms": round(fb_ms, 4), "fwd_bwd_unfused_ms": round(unfused_ms, 4),
             "plain_fft_ms": round(plain_ms, 4),
             "ratio_vs_4_plain": round(fb_ms / plain4, 3),
-            "gflops_equiv": round(4 * flops(N, rows) / (fb_ms * 1e-3) / 1e9, 1)}
+            "gflops_equiv": round(4 * flops(N, rows) / (fb_ms * 1e-3) / 1e9, 1),
+            "fused_step_ms": round(step_ms, 4),
+            "fused_step_ratio_vs_4_plain": round(step_ms / plain4, 3),
+            "fused_step_frac_hbm": round(28.0 * rows * N / (step_ms * 1e-3) / 1e9 / peaks()[0], 4)}
 
 
 def run_profile_case(args):

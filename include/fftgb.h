@@ -397,6 +397,33 @@ fft_status_t fft_filter_backward(fft_plan_t plan, const void *g_y, const void *H
                                  void *stream);
 
 /*
+ * fft_filter_step: one training step of the spectral filter under the
+ * masked-energy loss L = sum_{rows, k} mask * |y|^2 (mask real, one float per
+ * point), forward and backward fused.  One persistent kernel computes, per
+ * row: X = FFT(x); y = IFFT(X * H); the row's share of L; g_y = 2 mask y;
+ * g_z = FFT(g_y) / N; the grad_H partial sums conj(X) * g_z (in tensor
+ * memory); grad_x = F^H (conj(H) * g_z).  X and g_y never leave the SM, so
+ * a row moves 28 bytes per point (read x and mask, write y and grad_x).
+ * Then grad_H is summed over the CTAs by the same fixed-order tree as the
+ * backward's, and L over the CTAs in a fixed order in FP64 (both bitwise
+ * reproducible on a given GPU).
+ * plan: from fft_filter_plan with N in {8192, 16384} (FFT_ERR_NOT_SUPPORTED
+ *   for other N).  x, y, grad_x: batch*N float2; mask: batch*N float; H,
+ *   grad_H: N float2; loss: one float.  y may be NULL (not stored).  y and
+ *   grad_x may each equal x (a row is read before it is written) but may not
+ *   overlap anything else; mask, H, grad_H and loss may not overlap y or
+ *   grad_x (FFT_ERR_INVALID_VALUE).  Device pointers, 16-byte aligned (loss:
+ *   4-byte); asynchronous on stream.  batch 0: grad_H and loss are zeroed.
+ * The same results as fft_filter_forward, g_y = 2 mask y computed apart,
+ * and fft_filter_backward (to rounding).
+ * Paper: Sec. IX-A (FFT fused with matched filtering in one kernel) and
+ * Sec. II-D (SAR range compression); the loss and the backward pass have no
+ * counterpart in the paper.
+ */
+fft_status_t fft_filter_step(fft_plan_t plan, const void *x, const void *H, const float *mask,
+                             void *y, void *grad_x, void *grad_H, float *loss, void *stream);
+
+/*
  * fft_plan_columns — transforms down the columns of strided matrices without
  * a transpose: the azimuth pass (corner turn) of SAR processing over a
  * [azimuth, range] matrix stored range-contiguous (paper Sec. II-D, range and

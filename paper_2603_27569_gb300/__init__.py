@@ -12,7 +12,8 @@ import importlib as _importlib
 from ._binding import *  # noqa: F401,F403
 
 _TORCH_NAMES = ("Plan", "get_plan", "fft", "ifft", "fft_host", "SpectralFilter",
-                "spectral_filter", "clear_plan_cache", "ColumnPlan", "fft_columns")
+                "spectral_filter", "spectral_filter_step", "clear_plan_cache", "ColumnPlan",
+                "fft_columns")
 
 
 def __getattr__(name):

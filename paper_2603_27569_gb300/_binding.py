@@ -22,7 +22,7 @@ __all__ = [
     "fft_twiddle_table", "fft_twiddle_index", "fft_ragged_plan", "fft_autotune",
     "fft_autotune_load", "fft_autotune_clear", "fft_filter_apply",
     "fft_filter_grad_h_workspace", "fft_filter_grad_h", "fft_filter_plan",
-    "fft_filter_forward", "fft_filter_backward", "FFT_PATH_FILTER",
+    "fft_filter_forward", "fft_filter_backward", "fft_filter_step", "FFT_PATH_FILTER",
     "PlanInfo", "Config", "EXPORTED_SYMBOLS", "fft_list_configs", "fft_plan_config",
     "fft_fourstep_noalloc", "FFT_NOALLOC_MAX_POINTS", "fft_plan_columns", "FFT_PATH_COLUMNS",
     "FFT_PATH_TMEM_HALVES",
@@ -137,6 +137,7 @@ _SIGS = {
     "fft_filter_plan": ([ctypes.POINTER(_vp), _i32, _i64], _i32),
     "fft_filter_forward": ([_vp, _vp, _vp, _vp, _vp, _i32, _vp], _i32),
     "fft_filter_backward": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp], _i32),
+    "fft_filter_step": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _i32),
     "fft_list_configs": ([_i32, _vp, _i32], _i32),
     "fft_plan_config": ([ctypes.POINTER(_vp), _i32, _i64, _i32, _i32, ctypes.POINTER(Config)], _i32),
     "fft_fourstep_noalloc": ([_vp, _vp, _i32, _i64, _i32, _vp], _i32),
@@ -335,6 +336,12 @@ def fft_filter_forward(plan: int, x, H, y, X_save=None, conj_h: bool = False,
 def fft_filter_backward(plan: int, g_y, H, X_saved, grad_x, grad_H, stream=None) -> None:
     _check(lib().fft_filter_backward(plan, _ptr(g_y), _ptr(H), _ptr(X_saved), _ptr(grad_x),
                                      _ptr(grad_H), _stream(stream)), "fft_filter_backward")
+
+
+def fft_filter_step(plan: int, x, H, mask, y, grad_x, grad_H, loss, stream=None) -> None:
+    """Fused forward + masked-energy loss + backward (y may be None)."""
+    _check(lib().fft_filter_step(plan, _ptr(x), _ptr(H), _ptr(mask), _ptr(y), _ptr(grad_x),
+                                 _ptr(grad_H), _ptr(loss), _stream(stream)), "fft_filter_step")
 
 
 def fft_list_configs(N: int) -> list:

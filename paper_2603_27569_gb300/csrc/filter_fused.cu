@@ -407,6 +407,268 @@ filter_bwd2_kernel(FilterBwdArgs a) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(NCOL));
 }
 
+// Fused training step for the masked-energy loss L = sum m |y|^2 (m real,
+// one value per point), 32 points per thread, persistent like the backward.
+// Per row, four transforms on registers and the exchange buffer:
+//   half 1  X = F x; X into tensor memory; X * H into the buffer
+//   half 2  y = G (X * H); y stored (optional); L += m |y|^2;
+//           g_y = 2 m y into the buffer
+//   half 3  g_z = F g_y / N; sum += conj(X) * g_z (the grad_H partial sums,
+//           in tensor memory like the backward's); conj(H) * g_z into the buffer
+//   half 4  grad_x = F^H (conj(H) * g_z)   (filter_half_inv)
+// X never leaves the SM, and neither does g_y: a row reads x and m and writes
+// y and grad_x, 28 bytes per point against the 68 of forward, elementwise
+// gradient and backward as separate passes.  Tensor memory per CTA: the
+// backward's sum columns plus as many for X (256 columns at 8192, two CTAs
+// per SM; 512 at 16384, one).
+struct FilterStepArgs {
+  const float2 *x;
+  const float2 *H;
+  const float *mask;  // m, [batch][N]
+  float2 *y;          // nullable
+  float2 *gx;         // grad_x
+  float2 *partial;    // [gridDim.x][N] per-CTA grad_H sums
+  float *loss_part;   // [gridDim.x] per-CTA loss sums
+  const float2 *tw;
+  long long batch;
+  float inv_n;
+};
+
+template <int N, int P, class SC>
+__device__ __noinline__ void filter_half_fwd_stash(const float2 *src, const float2 *H, float2 *buf,
+                                                   const float2 *tw, int lt, uint32_t taddr_x) {
+  constexpr int T = N / P;
+  constexpr bool PL = pairable<N, P, SC>();
+  static_assert(P % 8 == 0, "the spectrum moves to tensor memory 8 points at a time");
+  float2 v[P];
+#pragma unroll
+  for (int m = 0; m < P; ++m) v[m] = __ldcs(src + lt + m * T);
+  run_passes<N, P, -1, SC, 0, SwizzledRow, 1, CtaBarrier, PL>(v, lt, buf, tw, SwizzledRow{});
+  // v[m] = X[out_index(lt, m)], the order half 3's transform leaves g_z in
+#pragma unroll
+  for (int c = 0; c < P / 8; ++c) {
+    float r[16];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      r[2 * q] = v[8 * c + q].x;
+      r[2 * q + 1] = v[8 * c + q].y;
+    }
+    tmem_st16(taddr_x + 16 * c, r);
+  }
+  if constexpr (PL) {
+#pragma unroll
+    for (int m = 0; m < P; m += 2) {
+      const float4 h = __ldg(reinterpret_cast<const float4 *>(H + out_index<N, P, SC, PL>(lt, m)));
+      v[m] = cmul(v[m], lo2(h));
+      v[m + 1] = cmul(v[m + 1], hi2(h));
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = cmul(v[m], __ldg(H + out_index<N, P, SC, PL>(lt, m)));
+  }
+  tmem_wait_st();
+  __syncthreads();  // every read of the buffer by the transform is done
+  if constexpr (PL) {
+#pragma unroll
+    for (int m = 0; m < P; m += 2)
+      *reinterpret_cast<float4 *>(buf + out_index<N, P, SC, PL>(lt, m)) = pack2(v[m], v[m + 1]);
+  } else {
+#pragma unroll
+    for (int m = 0; m < P; ++m) buf[out_index<N, P, SC, PL>(lt, m)] = v[m];
+  }
+}
+
+// Returns this thread's share of the row's loss.
+template <int N, int P, class SC>
+__device__ __noinline__ float filter_half_inv_loss(float2 *buf, float2 *y, const float *mask,
+                                                   const float2 *tw, int lt, float inv_n) {
+  constexpr int T = N / P;
+  constexpr bool PL = pairable<N, P, SC>();
+  float2 v[P];
+#pragma unroll
+  for (int m = 0; m < P; ++m) v[m] = buf[lt + m * T];
+  __syncthreads();  // every thread has its inputs: the transform may overwrite the buffer
+  run_passes<N, P, +1, SC, 0, SwizzledRow, 1, CtaBarrier, PL>(v, lt, buf, tw, SwizzledRow{});
+  // v[m] * inv_n = y[out_index(lt, m)]
+  float loss = 0.f;
+  if constexpr (PL) {
+#pragma unroll
+    for (int m = 0; m < P; m += 2) {
+      const int k = out_index<N, P, SC, PL>(lt, m);
+      const float2 a = cscale(v[m], inv_n), b = cscale(v[m + 1], inv_n);
+      if (y) __stcs(reinterpret_cast<float4 *>(y + k), pack2(a, b));
+      const float2 w = __ldcs(reinterpret_cast<const float2 *>(mask + k));
+      loss = fmaf(w.x, fmaf(a.x, a.x, a.y * a.y), loss);
+      loss = fmaf(w.y, fmaf(b.x, b.x, b.y * b.y), loss);
+      v[m] = cscale(a, 2.f * w.x);
+      v[m + 1] = cscale(b, 2.f * w.y);
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < P; ++m) {
+      const int k = out_index<N, P, SC, PL>(lt, m);
+      const float2 a = cscale(v[m], inv_n);
+      if (y) __stcs(y + k, a);
+      const float w = __ldcs(mask + k);
+      loss = fmaf(w, fmaf(a.x, a.x, a.y * a.y), loss);
+      v[m] = cscale(a, 2.f * w);
+    }
+  }
+  __syncthreads();  // every read of the buffer by the transform is done
+  if constexpr (PL) {
+#pragma unroll
+    for (int m = 0; m < P; m += 2)
+      *reinterpret_cast<float4 *>(buf + out_index<N, P, SC, PL>(lt, m)) = pack2(v[m], v[m + 1]);
+  } else {
+#pragma unroll
+    for (int m = 0; m < P; ++m) buf[out_index<N, P, SC, PL>(lt, m)] = v[m];
+  }
+  return loss;
+}
+
+template <int N, int P, class SC>
+__device__ __noinline__ void filter_half_bwd_buf(float2 *buf, const float2 *H, const float2 *tw,
+                                                 int lt, float inv_n, uint32_t taddr,
+                                                 uint32_t taddr_x) {
+  constexpr int T = N / P;
+  constexpr bool PL = pairable<N, P, SC>();
+  float2 v[P];
+#pragma unroll
+  for (int m = 0; m < P; ++m) v[m] = buf[lt + m * T];
+  __syncthreads();  // every thread has its inputs: the transform may overwrite the buffer
+  run_passes<N, P, -1, SC, 0, SwizzledRow, 1, CtaBarrier, PL>(v, lt, buf, tw, SwizzledRow{});
+#pragma unroll
+  for (int m = 0; m < P; ++m) v[m] = cscale(v[m], inv_n);  // g_z
+  // chunk c's sums and spectrum are read together, chunk c + 1's right
+  // after chunk c's store
+  float r[16], xr[16];
+  tmem_ld16(taddr, r);
+  tmem_ld16(taddr_x, xr);
+#pragma unroll
+  for (int c = 0; c < P / 8; ++c) {
+    tmem_wait_ld(r);
+    tmem_wait_ld(xr);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {  // sum += conj(X) g_z
+      const float2 g = v[8 * c + q];
+      const float xx = xr[2 * q], xy = xr[2 * q + 1];
+      r[2 * q] = fmaf(xx, g.x, fmaf(xy, g.y, r[2 * q]));
+      r[2 * q + 1] = fmaf(xx, g.y, fmaf(-xy, g.x, r[2 * q + 1]));
+    }
+    tmem_st16(taddr + 16 * c, r);
+    if (c + 1 < P / 8) {
+      tmem_ld16(taddr + 16 * (c + 1), r);
+      tmem_ld16(taddr_x + 16 * (c + 1), xr);
+    }
+  }
+  if constexpr (PL) {
+#pragma unroll
+    for (int m = 0; m < P; m += 2) {
+      const float4 h = __ldg(reinterpret_cast<const float4 *>(H + out_index<N, P, SC, PL>(lt, m)));
+      v[m] = cmulc(v[m], lo2(h));
+      v[m + 1] = cmulc(v[m + 1], hi2(h));
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = cmulc(v[m], __ldg(H + out_index<N, P, SC, PL>(lt, m)));
+  }
+  tmem_wait_st();
+  __syncthreads();  // every read of the buffer by the transform is done
+  if constexpr (PL) {
+#pragma unroll
+    for (int m = 0; m < P; m += 2)
+      *reinterpret_cast<float4 *>(buf + out_index<N, P, SC, PL>(lt, m)) = pack2(v[m], v[m + 1]);
+  } else {
+#pragma unroll
+    for (int m = 0; m < P; ++m) buf[out_index<N, P, SC, PL>(lt, m)] = v[m];
+  }
+}
+
+template <int N, int P, class SC>
+__global__ void __launch_bounds__(N / P, (65536 / ((N / P) * 128)) > 0 ? 65536 / ((N / P) * 128) : 1)
+filter_step_kernel(FilterStepArgs a) {
+  constexpr int T = N / P;
+  constexpr int WARPS = T / 32;
+  static_assert(T % 128 == 0, "whole warpgroups cover the tensor-memory lanes");
+  constexpr uint32_t NCOL = (WARPS / 4) * 64;  // the sums; as many again for X
+  static_assert(2 * NCOL <= 512, "sums and spectrum fit one SM's tensor memory");
+  extern __shared__ __align__(128) float2 smem[];
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + N);
+  float *red = reinterpret_cast<float *>(smem);  // the loss reduction, after the last row
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int lt = threadIdx.x, warp = lt >> 5;
+  if (warp == 0) tmem_alloc_warp(tslot, 2 * NCOL);
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  const uint32_t tbase = *tslot;
+  const uint32_t taddr = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * (warp >> 2));
+  const uint32_t taddr_x = taddr + NCOL;
+  {
+    float z[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) z[i] = 0.f;
+#pragma unroll
+    for (int c = 0; c < P / 8; ++c) tmem_st16(taddr + 16 * c, z);
+    tmem_wait_st();
+  }
+  float loss = 0.f;
+  for (long long row = blockIdx.x; row < a.batch; row += gridDim.x) {
+    const long long next = row + gridDim.x;
+    if (warp == 0 && next < a.batch) {  // the next row's x and mask into L2
+      prefetch_l2_warp(a.x + next * N, (long long)sizeof(float2) * N, lt);
+      prefetch_l2_warp(a.mask + next * N, (long long)sizeof(float) * N, lt);
+    }
+    filter_half_fwd_stash<N, P, SC>(a.x + row * N, a.H, smem, a.tw, lt, taddr_x);
+    __syncthreads();  // X * H is in the buffer
+    loss += filter_half_inv_loss<N, P, SC>(smem, a.y ? a.y + row * N : nullptr, a.mask + row * N,
+                                           a.tw, lt, a.inv_n);
+    __syncthreads();  // g_y is in the buffer
+    filter_half_bwd_buf<N, P, SC>(smem, a.H, a.tw, lt, a.inv_n, taddr, taddr_x);
+    __syncthreads();  // conj(H) g_z is in the buffer
+    filter_half_inv<N, P, SC>(smem, a.gx + row * N, a.tw, lt, 1, 1.0f);
+    __syncthreads();  // the next row rewrites the buffer
+  }
+  float2 *dst = a.partial + (size_t)blockIdx.x * N;
+#pragma unroll
+  for (int c = 0; c < P / 8; ++c) {
+    float r[16];
+    tmem_ld16(taddr + 16 * c, r);
+    tmem_wait_ld(r);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      dst[out_index<N, P, SC, pairable<N, P, SC>()>(lt, 8 * c + q)] =
+          make_float2(r[2 * q], r[2 * q + 1]);
+  }
+  // the CTA's loss: a fixed-order tree over the threads
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
+  if ((lt & 31) == 0) red[warp] = loss;
+  tmem_fence_before();
+  __syncthreads();
+  if (lt == 0) {
+    float s = 0.f;
+    for (int w = 0; w < WARPS; ++w) s += red[w];
+    a.loss_part[blockIdx.x] = s;
+  }
+  if (warp == 0) tmem_dealloc_warp(tbase, 2 * NCOL);
+}
+
+// L = the per-CTA loss sums added in a fixed pairwise order (in FP64).
+__global__ void __launch_bounds__(512) loss_tree_kernel(const float *part, int n, float *loss) {
+  __shared__ double s[512];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += 512) v += (double)part[i];
+  s[threadIdx.x] = v;
+  __syncthreads();
+  for (int h = 256; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *loss = (float)s[0];
+}
+
 struct FilterKernel {
   const void *fn;
   int threads, tb;
@@ -431,6 +693,7 @@ static FilterKernel make_kernel() {
 struct FilterVariant {
   FilterKernel fwd, spec, mulinv;  // fwd.fn == nullptr: the two-kernel forward
   FilterKernel bwd;                // one-kernel backward (32 points per thread), else nullptr
+  FilterKernel step;               // fused training step (32 points per thread), else nullptr
   KernelEntry sched;
 };
 
@@ -450,8 +713,15 @@ static FilterVariant variant() {
     v.bwd.threads = N / P;
     v.bwd.tb = 1;
     v.bwd.smem = sizeof(float2) * (size_t)N + 16;  // + the tensor-memory address slot
+    v.step.fn = (const void *)&filter_step_kernel<N, P, SC>;
+    v.step.threads = N / P;
+    v.step.tb = 1;
+    v.step.smem = v.bwd.smem;
   }
-  if constexpr (P < 32) v.bwd = FilterKernel{nullptr, 0, 0, 0};
+  if constexpr (P < 32) {
+    v.bwd = FilterKernel{nullptr, 0, 0, 0};
+    v.step = FilterKernel{nullptr, 0, 0, 0};
+  }
   v.spec = make_kernel<N, P, TB, SC, FM_SPEC>();
   v.mulinv = make_kernel<N, P, TB, SC, FM_MULINV>();
   v.sched = KernelEntry{};
@@ -479,11 +749,16 @@ struct FilterState {
                              // the one-kernel backward
   int bwd_grid = 0;          // CTAs of the one-kernel backward (resident on the GPU at once)
   int fwd_grid = 0;          // CTAs of the one-kernel forward (32 points per thread)
+  int step_grid = 0;         // CTAs of the fused training step (resident at once)
+  float *d_loss_part = nullptr;  // per-CTA loss sums of the training step
 };
 
 void filter_destroy(fft_plan_impl *pl) {
   FilterState *f = (FilterState *)pl->filter;
-  if (f) cudaFree(f->d_work);
+  if (f) {
+    cudaFree(f->d_work);
+    cudaFree(f->d_loss_part);
+  }
   delete f;
   pl->filter = nullptr;
 }
@@ -526,7 +801,7 @@ fft_status_t fft_filter_plan(fft_plan_t *out, int N, int64_t batch) {
     return fail(FFT_ERR_ALLOC);
   }
   cudaMemset(pl->d_status, 0, sizeof(int));
-  for (const FilterKernel *k : {&v.fwd, &v.spec, &v.mulinv, &v.bwd}) {
+  for (const FilterKernel *k : {&v.fwd, &v.spec, &v.mulinv, &v.bwd, &v.step}) {
     if (k->fn && k->smem > 48 * 1024 &&
         cudaFuncSetAttribute(k->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k->smem) !=
             cudaSuccess)
@@ -551,9 +826,16 @@ fft_status_t fft_filter_plan(fft_plan_t *out, int N, int64_t batch) {
       return fail(FFT_ERR_CUDA);
     f->fwd_grid = (int)std::min<int64_t>((int64_t)occ * sms, batch);
     const int tmem_cols = std::max(32, (v.bwd.threads / 128) * 64);
-    occ = std::min(occ, 512 / tmem_cols);
-    f->bwd_grid = (int)std::min<int64_t>((int64_t)occ * sms, batch);
-    work = std::max<int64_t>(work, (int64_t)f->bwd_grid * N * (int64_t)sizeof(float2));
+    f->bwd_grid = (int)std::min<int64_t>((int64_t)std::min(occ, 512 / tmem_cols) * sms, batch);
+    // the training step holds twice the columns (the sums and the spectrum)
+    f->step_grid =
+        (int)std::min<int64_t>((int64_t)std::min(occ, 512 / (2 * tmem_cols)) * sms, batch);
+    work = std::max<int64_t>(work, (int64_t)std::max(f->bwd_grid, f->step_grid) * N *
+                                       (int64_t)sizeof(float2));
+    if (dev_malloc(&f->d_loss_part, sizeof(float) * (size_t)f->step_grid) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(FFT_ERR_ALLOC);
+    }
   }
   if (work > 0 && dev_malloc(&f->d_work, (size_t)work) != cudaSuccess) {
     cudaGetLastError();
@@ -674,6 +956,58 @@ fft_status_t fft_filter_backward(fft_plan_t plan, const void *g_y, const void *H
   a.conj_h = 1;
   a.scale = 1.0f;
   return filter_launch(f->v.mulinv, a, st);
+}
+
+fft_status_t fft_filter_step(fft_plan_t plan, const void *x, const void *H, const float *mask,
+                             void *y, void *grad_x, void *grad_H, float *loss, void *stream) {
+  fft_status_t s = filter_check(plan, x, H, grad_x);
+  if (s != FFT_OK) return s;
+  if (!mask || !grad_H || !loss) return FFT_ERR_INVALID_VALUE;
+  if (((uintptr_t)mask | (uintptr_t)y | (uintptr_t)grad_H) & 15 || ((uintptr_t)loss & 3))
+    return FFT_ERR_MISALIGNED;
+  fft_plan_impl *pl = &plan->impl;
+  FilterState *f = (FilterState *)pl->filter;
+  if (!f->v.step.fn) return FFT_ERR_NOT_SUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int N = pl->N;
+  if (pl->batch == 0) {
+    if ((s = cuda_status(cudaMemsetAsync(grad_H, 0, sizeof(float2) * N, st))) != FFT_OK) return s;
+    return cuda_status(cudaMemsetAsync(loss, 0, sizeof(float), st));
+  }
+  const int64_t bytes = (int64_t)sizeof(float2) * N * pl->batch;
+  auto overlap = [](const void *p, int64_t pb, const void *q, int64_t qb) {
+    const char *a = (const char *)p, *b = (const char *)q;
+    return a < b + qb && b < a + pb;
+  };
+  // Outputs: y and grad_x may each be x itself (a CTA reads its row before it
+  // writes it) but overlap nothing else; the mask, H, grad_H and the loss
+  // overlap no output.
+  for (const void *o : {(const void *)y, (const void *)grad_x}) {
+    if (!o) continue;
+    if (o != x && overlap(o, bytes, x, bytes)) return FFT_ERR_INVALID_VALUE;
+    if (overlap(o, bytes, mask, bytes / 2) || overlap(o, bytes, H, sizeof(float2) * N) ||
+        overlap(o, bytes, grad_H, sizeof(float2) * N) || overlap(o, bytes, loss, sizeof(float)))
+      return FFT_ERR_INVALID_VALUE;
+  }
+  if (y && overlap(y, bytes, grad_x, bytes)) return FFT_ERR_INVALID_VALUE;
+  FilterStepArgs a{};
+  a.x = (const float2 *)x;
+  a.H = (const float2 *)H;
+  a.mask = mask;
+  a.y = (float2 *)y;
+  a.gx = (float2 *)grad_x;
+  a.partial = f->d_work;
+  a.loss_part = f->d_loss_part;
+  a.tw = pl->d_tw;
+  a.batch = pl->batch;
+  a.inv_n = 1.0f / (float)N;
+  void *args[] = {&a};
+  if ((s = cuda_status(launch_pdl(f->v.step.fn, dim3((unsigned)f->step_grid),
+                                  dim3(f->v.step.threads), f->v.step.smem, st, args))) != FFT_OK)
+    return s;
+  if ((s = grad_h_tree(f->d_work, (float2 *)grad_H, N, f->step_grid, st)) != FFT_OK) return s;
+  loss_tree_kernel<<<1, 512, 0, st>>>(f->d_loss_part, f->step_grid, loss);
+  return cuda_status(cudaGetLastError());
 }
 
 }  // extern "C"

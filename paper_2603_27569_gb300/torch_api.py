@@ -405,6 +405,29 @@ def spectral_filter(x: torch.Tensor, H: torch.Tensor, fused: bool | None = None)
     return _SpectralFilterFn.apply(x, H)
 
 
+def spectral_filter_step(x: torch.Tensor, H: torch.Tensor, mask: torch.Tensor,
+                         keep_y: bool = True):
+    """One fused training step of the filter under L = sum(mask * |y|^2):
+    returns (y or None, L, grad_x, grad_H) from one persistent kernel per call
+    (C ABI: fft_filter_step; N = 8192 or 16384, x [..., N] complex64, mask the
+    same shape as float32)."""
+    N = x.shape[-1]
+    batch = x.numel() // N
+    xc = x.contiguous()
+    Hc = H.detach().contiguous()
+    m = mask.to(torch.float32).contiguous()
+    if m.shape != x.shape:
+        raise ValueError("mask must have x's shape")
+    plan = _filter_plan(N, batch, x.device)
+    y = torch.empty_like(xc) if keep_y else None
+    gx = torch.empty_like(xc)
+    gH = torch.empty(N, dtype=torch.complex64, device=x.device)
+    loss = torch.empty((), dtype=torch.float32, device=x.device)
+    B.fft_filter_step(plan.handle, xc, Hc, m, y, gx, gH, loss,
+                      torch.cuda.current_stream(x.device))
+    return (y.view(x.shape) if keep_y else None), loss, gx.view(x.shape), gH
+
+
 class SpectralFilter(torch.nn.Module):
     """Learnable matched filter H (complex64 [N]) applied in the frequency domain."""
 

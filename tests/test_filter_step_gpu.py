@@ -1,0 +1,136 @@
+"""The fused training step of the spectral filter (fft_filter_step): forward,
+the masked-energy loss L = sum m |y|^2 and the backward in one persistent
+kernel.  y, L, grad_x and grad_H are compared with the oracle (whose analytic
+gradient is pinned to FP64 central differences in test_oracle.py), with the
+separate forward / elementwise / backward path, and run to run."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2603_27569_gb300 as fg
+from paper_2603_27569_gb300 import synth
+from gpu_util import TOL_FP32, TOL_GRAD, rel_l2_rows, to_dev, to_host
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+INVALID_VALUE, NOT_SUPPORTED = 2, 7
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2603_27569_gb300 import build
+
+    build.build()
+
+
+def rel(a, b):
+    a = np.asarray(a, np.complex128)
+    b = np.asarray(b, np.complex128)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def sar_case(rows, N, Np, seed=0):
+    x, pulse = synth.sar_echoes(rows, N, Np=Np, seed=seed)
+    H = np.conj(oracle.fft(pulse)).astype(np.complex64)
+    m = synth.real_mask((rows, N), seed=seed + 2)
+    return x, H, m
+
+
+def step(x, H, m, keep_y=True):
+    y, loss, gx, gH = fg.spectral_filter_step(to_dev(x), to_dev(H), to_dev(m), keep_y=keep_y)
+    torch.cuda.synchronize()
+    return (to_host(y) if keep_y else None), float(loss), to_host(gx), to_host(gH)
+
+
+# 5 and 3 rows: fewer rows than CTAs; 400 and 160: more rows than the
+# resident grid (304 CTAs at 8192, 152 at 16384), so CTAs take 1 or 2 rows
+@pytest.mark.parametrize("rows,N,Np", [(5, 8192, 2048), (400, 8192, 2048), (3, 16384, 4096),
+                                       (160, 16384, 4096)])
+def test_fused_step_matches_oracle(rows, N, Np):
+    x, H, m = sar_case(rows, N, Np, seed=rows)
+    y, loss, gx, gH = step(x, H, m)
+    assert rel_l2_rows(y, oracle.spectral_filter_forward(x, H)).max() <= 2 * TOL_FP32
+    want_loss = oracle.spectral_filter_loss(x, H, m)
+    assert abs(loss - want_loss) <= 1e-5 * abs(want_loss)
+    ogx, ogH = oracle.spectral_filter_grads(x, H, m)
+    assert rel(gx, ogx) <= TOL_GRAD
+    assert rel(gH, ogH) <= TOL_GRAD
+
+
+def test_fused_step_agrees_with_the_separate_passes():
+    """y is bitwise the fused forward's (same arithmetic); L, grad_x and
+    grad_H agree with forward + torch's 2 m y + backward to rounding."""
+    rows, N = 64, 8192
+    x, H, m = sar_case(rows, N, 2048, seed=11)
+    y, loss, gx, gH = step(x, H, m)
+    xd = to_dev(x).requires_grad_(True)
+    layer = fg.SpectralFilter(to_dev(H), fused=True)
+    yd = layer(xd)
+    ld = (to_dev(m) * (yd.real ** 2 + yd.imag ** 2)).sum()
+    ld.backward()
+    torch.cuda.synchronize()
+    assert np.array_equal(y.view(np.uint32), to_host(yd.detach()).view(np.uint32))
+    assert abs(loss - float(ld.detach())) <= 1e-5 * abs(loss)
+    assert rel(gx, to_host(xd.grad)) <= 2e-6
+    assert rel(gH, to_host(layer.H.grad)) <= 2e-6
+
+
+def test_fused_step_without_y_in_place_and_reproducible():
+    rows, N = 40, 16384
+    x, H, m = sar_case(rows, N, 4096, seed=3)
+    y1, l1, gx1, gH1 = step(x, H, m)
+    y2, l2, gx2, gH2 = step(x, H, m, keep_y=False)
+    assert y2 is None
+    assert l1 == l2
+    assert np.array_equal(gx1.view(np.uint32), gx2.view(np.uint32))
+    assert np.array_equal(gH1.view(np.uint32), gH2.view(np.uint32))
+    # grad_x written over x
+    plan = fg.fft_filter_plan(N, rows)
+    xd, Hd, md = to_dev(x), to_dev(H), to_dev(m)
+    gH = torch.empty(N, dtype=torch.complex64, device="cuda")
+    loss = torch.empty((), dtype=torch.float32, device="cuda")
+    fg.fft_filter_step(plan, xd, Hd, md, None, xd, gH, loss, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    fg.fft_destroy(plan)
+    assert np.array_equal(to_host(xd).view(np.uint32), gx1.view(np.uint32))
+    assert np.array_equal(to_host(gH).view(np.uint32), gH1.view(np.uint32))
+    assert float(loss) == l1
+
+
+def test_fused_step_edge_cases():
+    L = fg.lib()
+    st = torch.cuda.current_stream()
+    # batch 0: grad_H and the loss are zeroed
+    plan = fg.fft_filter_plan(8192, 0)
+    buf = torch.ones(8192, dtype=torch.complex64, device="cuda")
+    H = torch.ones(8192, dtype=torch.complex64, device="cuda")
+    m = torch.ones(8192, dtype=torch.float32, device="cuda")
+    gH = torch.full((8192,), 3.0 + 1j, dtype=torch.complex64, device="cuda")
+    loss = torch.full((), 5.0, dtype=torch.float32, device="cuda")
+    fg.fft_filter_step(plan, buf, H, m, None, buf, gH, loss, st)
+    torch.cuda.synchronize()
+    fg.fft_destroy(plan)
+    assert float(loss) == 0.0 and not bool(gH.abs().sum())
+    # N without the 32-point kernels: not supported
+    plan = fg.fft_filter_plan(4096, 2)
+    x = torch.zeros(2 * 4096, dtype=torch.complex64, device="cuda")
+    rc = L.fft_filter_step(plan, x.data_ptr(), H.data_ptr(), m.data_ptr(), None, x.data_ptr(),
+                           gH.data_ptr(), loss.data_ptr(), None)
+    fg.fft_destroy(plan)
+    assert rc == NOT_SUPPORTED
+    # y overlapping grad_x, and grad_x overlapping the mask: refused
+    rows, N = 4, 8192
+    plan = fg.fft_filter_plan(N, rows)
+    x = torch.zeros(rows * N, dtype=torch.complex64, device="cuda")
+    big = torch.zeros(3 * rows * N, dtype=torch.complex64, device="cuda")
+    mk = torch.zeros(rows * N, dtype=torch.float32, device="cuda")
+    y, gx = big[: rows * N], big[rows * N // 2: rows * N // 2 + rows * N]
+    rc = L.fft_filter_step(plan, x.data_ptr(), H.data_ptr(), mk.data_ptr(), y.data_ptr(),
+                           gx.data_ptr(), gH.data_ptr(), loss.data_ptr(), None)
+    assert rc == INVALID_VALUE
+    gx2 = big[rows * N:]
+    rc = L.fft_filter_step(plan, x.data_ptr(), H.data_ptr(), gx2.data_ptr(), None,
+                           gx2.data_ptr(), gH.data_ptr(), loss.data_ptr(), None)
+    fg.fft_destroy(plan)
+    assert rc == INVALID_VALUE
