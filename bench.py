@@ -940,6 +940,15 @@ def run_profile_case(args):
             fg.fft_exec(h, xr, yr, st)
         info = fg.fft_plan_info(h)
         fg.fft_destroy(h)
+    elif kind == "filter_step":
+        # the config's shape [4096, 8192] (x 256 MiB, mask 128 MiB, y and grad_x)
+        rows = 4096 if N == 8192 else POINTS // N
+        xs = torch.randn(rows, N, dtype=torch.complex64, device="cuda")
+        H = torch.randn(N, dtype=torch.complex64, device="cuda")
+        m = torch.rand(rows, N, dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            fg.spectral_filter_step(xs, H, m)
+        info = {"rows": rows}
     elif kind == "columns":
         p = fg.ColumnPlan(N, batch, 1, direction=args.profile_direction, flags=args.profile_flags)
         for _ in range(3):
@@ -976,7 +985,8 @@ def main():
     ap.add_argument("--profile-direction", type=int, default=-1, choices=[-1, 1],
                     help="direction of the profiled plan (kind plan)")
     ap.add_argument("--profile-kind", default="plan",
-                    choices=["plan", "tc", "filter_fwd", "filter_bwd", "ragged", "columns"])
+                    choices=["plan", "tc", "filter_fwd", "filter_bwd", "filter_step", "ragged",
+                             "columns"])
     ap.add_argument("--profile-config", type=str, default="",
                     help="JSON of one fft_list_configs entry to force")
     args = ap.parse_args()
