@@ -108,7 +108,8 @@ typedef struct {
     int threads_per_cta;
     int num_passes;         /* exchange passes of the (first) kernel          */
     int radix[8];           /* radix of each pass, first pass first           */
-    int n1, n2;             /* four-step split N = n1 * n2 (0 otherwise)       */
+    int n1, n2;             /* four-step split N = n1 * n2, or a column plan's
+                               two-launch split L = n1 * n2 (0 otherwise)     */
     int64_t scratch_bytes;  /* device scratch owned by the plan               */
     int twiddle_mode;       /* as in fft_config_t                              */
     int grid_ctas;          /* CTAs launched per exec (0 = one per tile)      */
@@ -159,8 +160,9 @@ const char *fft_status_string(fft_status_t status);
  * decimation-in-frequency split into two 16384-point halves on one SM, one
  * half held in tensor memory while the other transforms; one persistent
  * 512-thread CTA per SM).  Above that the two-phase four-step runs
- * (N = n1 * n2 with a phase-1 length n2 <= 256 and a phase-2 length
- * n1 <= 4096; its intermediate doubles the HBM traffic).  Rows on
+ * (N = n1 * n2 with a phase-1 length n2 of 256 up to 2^17 and 512 above,
+ * and a phase-2 length n1 <= 4096; its intermediate doubles the HBM
+ * traffic).  Rows on
  * thread-block clusters (cluster_split in fft_config_t, N = 8192 .. 65536)
  * and the four-step at 32768 are selectable through fft_plan_config.
  * batch >= 0 (0 makes a valid plan whose
