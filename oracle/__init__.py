@@ -135,26 +135,27 @@ def ifft(x, nthreads: int = 1) -> np.ndarray:
 #   grad_H = sum_rows conj(FFT(x)) * g_z
 #   grad_x = F^H (conj(H) * g_z) = N * IFFT(conj(H) * g_z)
 # --------------------------------------------------------------------------
-def spectral_filter_forward(x, H):
-    X = fft(x)
+# nthreads only spreads rows over threads; the arithmetic is the same.
+def spectral_filter_forward(x, H, nthreads: int = 1):
+    X = fft(x, nthreads=nthreads)
     z = X * _as_c128(H)
-    return ifft(z)
+    return ifft(z, nthreads=nthreads)
 
 
-def spectral_filter_loss(x, H, m) -> float:
-    y = spectral_filter_forward(x, H)
+def spectral_filter_loss(x, H, m, nthreads: int = 1) -> float:
+    y = spectral_filter_forward(x, H, nthreads=nthreads)
     return float(np.sum(np.asarray(m, dtype=np.float64) * (y.real ** 2 + y.imag ** 2)))
 
 
-def spectral_filter_grads(x, H, m):
+def spectral_filter_grads(x, H, m, nthreads: int = 1):
     x = _as_c128(x)
     H = _as_c128(H)
     m = np.asarray(m, dtype=np.float64)
     N = x.shape[-1]
-    X = fft(x)
-    y = ifft(X * H)
+    X = fft(x, nthreads=nthreads)
+    y = ifft(X * H, nthreads=nthreads)
     g_y = 2.0 * m * y
-    g_z = fft(g_y) / N
+    g_z = fft(g_y, nthreads=nthreads) / N
     grad_H = np.sum(np.conj(X) * g_z, axis=tuple(range(x.ndim - 1)))
-    grad_x = N * ifft(np.conj(H) * g_z)
+    grad_x = N * ifft(np.conj(H) * g_z, nthreads=nthreads)
     return grad_x, grad_H

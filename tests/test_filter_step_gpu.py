@@ -9,7 +9,7 @@ import pytest
 import oracle
 import paper_2603_27569_gb300 as fg
 from paper_2603_27569_gb300 import synth
-from gpu_util import TOL_FP32, TOL_GRAD, rel_l2_rows, to_dev, to_host
+from gpu_util import NTHREADS, TOL_FP32, TOL_GRAD, rel_l2_rows, to_dev, to_host
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -56,6 +56,34 @@ def test_fused_step_matches_oracle(rows, N, Np):
     ogx, ogH = oracle.spectral_filter_grads(x, H, m)
     assert rel(gx, ogx) <= TOL_GRAD
     assert rel(gH, ogH) <= TOL_GRAD
+
+
+def test_fused_step_at_the_full_config_size():
+    """The spectral-filter config itself: [4096, 8192] chirp echoes (reference
+    pulse of 2048 samples), H = conj FFT of the pulse, mask U[0, 1) seed 2, in
+    the launch the bench times (one resident grid, ~13 rows per CTA): y on
+    sampled rows, L, grad_x and grad_H in full against the oracle."""
+    rows, N = 4096, 8192
+    x, pulse = synth.sar_echoes(rows, N, Np=2048, seed=0)
+    H = np.conj(oracle.fft(pulse)).astype(np.complex64)
+    m = synth.real_mask((rows, N), seed=2)
+    y, loss, gx, gH = step(x, H, m)
+    sample = np.random.default_rng(7).choice(rows, 24, replace=False)
+    assert rel_l2_rows(y[sample], oracle.spectral_filter_forward(x[sample], H)).max() <= 2 * TOL_FP32
+    want_loss = oracle.spectral_filter_loss(x, H, m, nthreads=NTHREADS)
+    assert abs(loss - want_loss) <= 1e-5 * abs(want_loss)
+    ogx, ogH = oracle.spectral_filter_grads(x, H, m, nthreads=NTHREADS)
+    assert rel(gx, ogx) <= TOL_GRAD
+    assert rel(gH, ogH) <= TOL_GRAD
+    # the autograd layer (one-kernel forward, torch's 2 m y, one-kernel
+    # backward) on the same data
+    xd = to_dev(x).requires_grad_(True)
+    layer = fg.SpectralFilter(to_dev(H), fused=True)
+    yd = layer(xd)
+    (to_dev(m) * (yd.real ** 2 + yd.imag ** 2)).sum().backward()
+    torch.cuda.synchronize()
+    assert rel(to_host(xd.grad), ogx) <= TOL_GRAD
+    assert rel(to_host(layer.H.grad), ogH) <= TOL_GRAD
 
 
 def test_fused_step_agrees_with_the_separate_passes():
