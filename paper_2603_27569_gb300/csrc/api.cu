@@ -1178,7 +1178,9 @@ fft_status_t fft_plan_columns(fft_plan_t *out, int L, int64_t ncols, int64_t nma
     if (nmat * n1 * (ncols / k1->TB) > 0x7fffffffLL || nmat * n2 * (ncols / k->TB) > 0x7fffffffLL)
       return FFT_ERR_INVALID_SIZE;
     const int64_t mat_bytes = (int64_t)sizeof(float2) * L * ncols;
-    chunk = std::max<int64_t>(1, std::min<int64_t>(nmat, kColumnScratchBytes / std::max<int64_t>(1, mat_bytes)));
+    if (nmat > 0)
+      chunk = std::max<int64_t>(
+          1, std::min<int64_t>(nmat, kColumnScratchBytes / std::max<int64_t>(1, mat_bytes)));
   }
   fft_plan_s *h = new (std::nothrow) fft_plan_s;
   if (!h) return FFT_ERR_ALLOC;

@@ -153,6 +153,14 @@ def test_long_strided_columns_match_oracle(L, direction):
         assert np.all(out[mask] == complex(7.0, -7.0))
 
 
+def test_long_column_plan_without_matrices():
+    plan = fg.ColumnPlan(16384, 64, 0)
+    assert plan.info()["scratch_bytes"] == 0
+    x = torch.zeros(16, dtype=torch.complex64, device="cuda")
+    fg.fft_exec(plan.handle, x, x, None)     # nothing to do
+    plan.close()
+
+
 def test_longest_column():
     L, ncols = 1 << 21, 16
     x = synth.gaussian((1, L, ncols), seed=21)
