@@ -452,6 +452,7 @@ fft_status_t exec_rows(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t
     c1.ncols = pl->n1;
     c1.ntot = pl->N;
     c1.scale = 1.f;
+    c1.in_extent = c1.out_extent = rows * pl->N;
     fft_status_t s = launch_column(pl->k_col1, pl->direction, c1, st);
     if (s != FFT_OK) return s;
     ColumnArgs c2{};
@@ -467,6 +468,7 @@ fft_status_t exec_rows(fft_plan_impl *pl, const float2 *in, float2 *out, int64_t
     c2.ncols = pl->n2;
     c2.ntot = pl->N;
     c2.scale = pl->scale;
+    c2.in_extent = c2.out_extent = rows * pl->N;
     return launch_column(pl->k_col2, pl->direction, c2, st);
   }
   if (pl->path == FFT_PATH_TENSORCORE) return tc_exec(pl, in, out, rows, st);
@@ -681,6 +683,7 @@ static fft_status_t exec_long_columns(fft_plan_impl *pl, const float2 *in, float
   const int64_t rs = pl->col_row_stride, ms = pl->col_mat_stride;
   for (int64_t m0 = 0; m0 < pl->col_nmat; m0 += pl->col_chunk) {
     const int64_t nm = std::min(pl->col_chunk, pl->col_nmat - m0);
+    const int64_t user_extent = (nm - 1) * ms + (L - 1) * rs + nc;  // elements of this chunk
     ColumnArgs c1{};
     c1.in = in + m0 * ms;
     c1.out = pl->d_scratch;
@@ -697,6 +700,8 @@ static fft_status_t exec_long_columns(fft_plan_impl *pl, const float2 *in, float
     c1.ncols = (int)nc;
     c1.ntot = (int)L;
     c1.scale = 1.0f;
+    c1.in_extent = user_extent;
+    c1.out_extent = nm * L * nc;
     fft_status_t s = launch_column(pl->k_col1, pl->direction, c1, st);
     if (s != FFT_OK) return s;
     ColumnArgs c2{};
@@ -714,6 +719,8 @@ static fft_status_t exec_long_columns(fft_plan_impl *pl, const float2 *in, float
     c2.ncols = (int)nc;
     c2.ntot = (int)L;
     c2.scale = pl->scale;
+    c2.in_extent = nm * L * nc;
+    c2.out_extent = user_extent;
     s = launch_column(pl->k_col2, pl->direction, c2, st);
     if (s != FFT_OK) return s;
   }
@@ -1043,6 +1050,7 @@ fft_status_t fft_exec(fft_plan_t plan, const void *in, void *out, void *stream) 
     c.ncols = (int)pl->col_ncols;
     c.ntot = 0;  // no four-step twiddle on this path
     c.scale = pl->scale;
+    c.in_extent = c.out_extent = extent / (int64_t)sizeof(float2);
     return launch_column(pl->k_col2, pl->direction, c, (cudaStream_t)stream);
   }
   if (pl->batch == 0) return FFT_OK;

@@ -39,6 +39,9 @@ enum BoundsSite {
   kSiteTwiddle = 5,     // pass-table entry
   kSiteXchgWrite = 6,   // exchange write: logical index, then buffer slot
   kSiteXchgRead = 7,    // exchange read: logical index, then buffer slot
+  kSiteColLoad = 8,     // column kernel: global load (offset in the input extent)
+  kSiteColStore = 9,    // column kernel: global store (offset in the output extent)
+  kSiteColTwiddle = 10, // column kernel: per-sub-matrix twiddle entry
   kSiteSelfTest = 99,   // fft_debug_bounds_selftest
 };
 

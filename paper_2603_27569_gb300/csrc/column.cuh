@@ -48,6 +48,7 @@ struct ColumnArgs {
   long long in_mat_stride, out_mat_stride;  // elements between matrices
   long long in_sub_stride, out_sub_stride;  // elements between sub-matrices
   int nsub;              // sub-matrices per matrix (0 and 1: one)
+  long long in_extent, out_extent;  // elements reachable from in / out (bounds-check build)
   int in_row_stride;     // elements between consecutive rows of the input
   int out_row_stride;    // elements between rows of a non-transposed output
   int ncols;             // columns per matrix (multiple of C)
@@ -85,9 +86,14 @@ column_kernel(ColumnArgs args) {
   }
   float2 a[P];
   {
-    const float2 *src = args.in + mat * args.in_mat_stride + sub * args.in_sub_stride + c0 + c;
+    const long long base = mat * args.in_mat_stride + sub * args.in_sub_stride + c0 + c;
+    const float2 *src = args.in + base;
 #pragma unroll
-    for (int m = 0; m < P; ++m) a[m] = __ldg(src + (long long)(lt + m * T) * args.in_row_stride);
+    for (int m = 0; m < P; ++m) {
+      const long long off = (long long)(lt + m * T) * args.in_row_stride;
+      a[m] = FFTGB_OK(base + off, args.in_extent, kSiteColLoad) ? __ldg(src + off)
+                                                               : make_float2(0.f, 0.f);
+    }
   }
   run_passes<L, P, D, SC, 0>(a, lt, smem, args.tw, Interleaved<C>{c});
   // a[m] now holds output index final_index(lt, m) of column c0 + c.
@@ -104,8 +110,11 @@ column_kernel(ColumnArgs args) {
     // most two adjacent entries per load (all C columns share k).
     const float2 *tw = args.tw_a + sub * L;
 #pragma unroll
-    for (int m = 0; m < P; ++m)
-      a[m] = cmul_dir<D>(a[m], __ldg(tw + final_index<L, P, SC>(lt, m)));
+    for (int m = 0; m < P; ++m) {
+      const int k = final_index<L, P, SC>(lt, m);
+      if (FFTGB_OK(sub * L + k, (long long)(args.nsub > 1 ? args.nsub : 1) * L, kSiteColTwiddle))
+        a[m] = cmul_dir<D>(a[m], __ldg(tw + k));
+    }
   }
   if constexpr (TRANSPOSED) {
     // out[col * L + k]: stage through a tile padded to C + 1 columns.
@@ -114,18 +123,23 @@ column_kernel(ColumnArgs args) {
 #pragma unroll
     for (int m = 0; m < P; ++m) smem[final_index<L, P, SC>(lt, m) * LD + c] = a[m];
     __syncthreads();
-    float2 *dst = args.out + mat * args.out_mat_stride + (long long)c0 * L;
+    const long long base = mat * args.out_mat_stride + (long long)c0 * L;
+    float2 *dst = args.out + base;
 #pragma unroll
     for (int u = 0; u < P; ++u) {
       const int e = threadIdx.x + u * NT;  // e = col_local * L + k
       const int cl = e / L, k = e - cl * L;
-      dst[e] = cscale(smem[k * LD + cl], args.scale);
+      if (FFTGB_OK(base + e, args.out_extent, kSiteColStore))
+        dst[e] = cscale(smem[k * LD + cl], args.scale);
     }
   } else {
-    float2 *dst = args.out + mat * args.out_mat_stride + sub * args.out_sub_stride + c0 + c;
+    const long long base = mat * args.out_mat_stride + sub * args.out_sub_stride + c0 + c;
+    float2 *dst = args.out + base;
 #pragma unroll
-    for (int m = 0; m < P; ++m)
-      dst[(long long)final_index<L, P, SC>(lt, m) * args.out_row_stride] = cscale(a[m], args.scale);
+    for (int m = 0; m < P; ++m) {
+      const long long off = (long long)final_index<L, P, SC>(lt, m) * args.out_row_stride;
+      if (FFTGB_OK(base + off, args.out_extent, kSiteColStore)) dst[off] = cscale(a[m], args.scale);
+    }
   }
 }
 

@@ -243,6 +243,7 @@ extern "C" fft_status_t fft_fourstep_noalloc(const void *in, void *out, int N, i
   c1.ncols = z.n1;
   c1.ntot = N;
   c1.scale = 1.f;
+  c1.in_extent = c1.out_extent = (long long)batch * N;
   s = launch_column(z.k1, direction, c1, st);
   if (s != FFT_OK) return s;
   ColumnArgs c2{};
@@ -257,5 +258,6 @@ extern "C" fft_status_t fft_fourstep_noalloc(const void *in, void *out, int N, i
   c2.ncols = z.n2;
   c2.ntot = N;
   c2.scale = direction == FFT_INVERSE ? 1.0f / (float)N : 1.0f;
+  c2.in_extent = c2.out_extent = (long long)batch * N;
   return launch_column(z.k2, direction, c2, st);
 }
