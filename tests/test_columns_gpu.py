@@ -237,3 +237,21 @@ def test_forced_routes_at_2048_and_4096(L):
             plan.close()
             err = col_err(got, column_oracle(x, direction > 0))
             assert err.max() <= TOL_FP32, (flags, direction, err.max())
+
+
+@pytest.mark.parametrize("L,flags", [(1024, 0), (2048, 0), (4096, 0), (4096, fg.FFT_FLAG_FORCE_SINGLE_CTA),
+                                     (16384, 0), (65536, 0)])
+def test_bench_column_workload_sampled(L, flags):
+    """The bench's azimuth workload: one contiguous [L, 2^25 / L] matrix (256
+    MiB), in the launch the bench times; sampled columns against the oracle."""
+    ncols = (1 << 25) // L
+    g = torch.Generator(device="cuda").manual_seed(L)
+    xd = torch.randn((L, ncols), dtype=torch.complex64, device="cuda", generator=g)
+    plan = fg.ColumnPlan(L, ncols, 1, flags=flags)
+    yd = plan(xd)
+    torch.cuda.synchronize()
+    plan.close()
+    cols = np.unique(np.r_[0, 1, ncols - 1, np.random.default_rng(L).choice(ncols, 13)])
+    x = xd[:, cols].cpu().numpy().T
+    y = yd[:, cols].cpu().numpy().T
+    assert rel_l2_rows(y, oracle.fft(x, nthreads=NTHREADS)).max() <= TOL_FP32
