@@ -409,8 +409,9 @@ fft_status_t fft_filter_backward(fft_plan_t plan, const void *g_y, const void *H
  * Then grad_H is summed over the CTAs by the same fixed-order tree as the
  * backward's, and L over the CTAs in a fixed order in FP64 (both bitwise
  * reproducible on a given GPU).
- * plan: from fft_filter_plan with N in {8192, 16384} (FFT_ERR_NOT_SUPPORTED
- *   for other N).  x, y, grad_x: batch*N float2; mask: batch*N float; H,
+ * plan: from fft_filter_plan (N = 256..16384; below 8192 the kernel takes
+ *   TB = 4096 / N rows per CTA and adds its rows' sums before the tree).
+ *   x, y, grad_x: batch*N float2; mask: batch*N float; H,
  *   grad_H: N float2; loss: one float.  y may be NULL (not stored).  y and
  *   grad_x may each equal x (a row is read before it is written) but may not
  *   overlap anything else; mask, H, grad_H and loss may not overlap y or

@@ -655,6 +655,178 @@ filter_step_kernel(FilterStepArgs a) {
   if (warp == 0) tmem_dealloc_warp(tbase, 2 * NCOL);
 }
 
+// The training step for 16 points per thread (N <= 4096): TB rows per CTA,
+// X and the grad_H sums in tensor memory (32 + 32 columns per thread lane).
+// Thread lt holds point lt + m T after every transform, which is what the
+// next one reads.  The four transforms inlined into one body spill ~0.5 KiB
+// per thread, so, as for 32 points, two separately compiled halves of two
+// transforms each meet through the exchange buffer (g_y at lt + m T).  At the
+// end the CTA's TB row slots are added in slot order through the buffer, one
+// partial row per CTA for the same tree as above.
+template <int N, int P, class SC>
+__device__ __noinline__ float step_small_front(const float2 *src, int active, const float2 *H,
+                                               const float *mk, float2 *yd, float2 *buf,
+                                               const float2 *tw, int lt, float inv_n,
+                                               uint32_t taddr_x) {
+  constexpr int T = N / P;
+  static_assert(P == 16, "four 8-column moves of tensor memory per thread");
+  float2 v[P];
+#pragma unroll
+  for (int m = 0; m < P; ++m) v[m] = active ? __ldcs(src + lt + m * T) : make_float2(0.f, 0.f);
+  run_passes<N, P, -1, SC, 0, SwizzledRow, 1>(v, lt, buf, tw, SwizzledRow{});
+  // v[m] = X[lt + m T]: into tensor memory, then X * H
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    float r[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      r[2 * q] = v[4 * c + q].x;
+      r[2 * q + 1] = v[4 * c + q].y;
+    }
+    tmem_st8(taddr_x + 8 * c, r);
+  }
+#pragma unroll
+  for (int m = 0; m < P; ++m) v[m] = cmul(v[m], __ldg(H + lt + m * T));
+  tmem_wait_st();
+  __syncthreads();  // the forward's last exchange is read
+  run_passes<N, P, +1, SC, 0, SwizzledRow, 1>(v, lt, buf, tw, SwizzledRow{});
+  // v[m] / N = y[lt + m T]; L += m |y|^2; g_y = 2 m y
+  float loss = 0.f;
+#pragma unroll
+  for (int m = 0; m < P; ++m) {
+    const int k = lt + m * T;
+    const float2 yv = cscale(v[m], inv_n);
+    if (active && yd) __stcs(yd + k, yv);
+    const float w = active ? __ldcs(mk + k) : 0.f;
+    loss = fmaf(w, fmaf(yv.x, yv.x, yv.y * yv.y), loss);
+    v[m] = cscale(yv, 2.f * w);
+  }
+  __syncthreads();  // the inverse's last exchange is read
+#pragma unroll
+  for (int m = 0; m < P; ++m) buf[lt + m * T] = v[m];
+  return loss;
+}
+
+template <int N, int P, class SC>
+__device__ __noinline__ void step_small_back(float2 *gd, int active, const float2 *H, float2 *buf,
+                                             const float2 *tw, int lt, float inv_n,
+                                             uint32_t taddr, uint32_t taddr_x) {
+  constexpr int T = N / P;
+  float2 v[P];
+#pragma unroll
+  for (int m = 0; m < P; ++m) v[m] = buf[lt + m * T];
+  __syncthreads();  // every thread has its g_y: the transform may overwrite the buffer
+  run_passes<N, P, -1, SC, 0, SwizzledRow, 1>(v, lt, buf, tw, SwizzledRow{});
+  // g_z = v / N; sums += conj(X) g_z, four points (8 columns) at a time
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    float r[8], xr[8];
+    tmem_ld8(taddr + 8 * c, r);
+    tmem_ld8(taddr_x + 8 * c, xr);
+    tmem_wait_ld(r);
+    tmem_wait_ld(xr);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float2 g = cscale(v[4 * c + q], inv_n);
+      const float xx = xr[2 * q], xy = xr[2 * q + 1];
+      r[2 * q] = fmaf(xx, g.x, fmaf(xy, g.y, r[2 * q]));
+      r[2 * q + 1] = fmaf(xx, g.y, fmaf(-xy, g.x, r[2 * q + 1]));
+      v[4 * c + q] = g;
+    }
+    tmem_st8(taddr + 8 * c, r);
+  }
+#pragma unroll
+  for (int m = 0; m < P; ++m) v[m] = cmulc(v[m], __ldg(H + lt + m * T));
+  tmem_wait_st();
+  __syncthreads();  // the forward's last exchange is read
+  run_passes<N, P, +1, SC, 0, SwizzledRow, 1>(v, lt, buf, tw, SwizzledRow{});
+  if (active) {
+#pragma unroll
+    for (int m = 0; m < P; ++m) __stcs(gd + lt + m * T, v[m]);
+  }
+}
+
+template <int N, int P, int TB, class SC>
+__global__ void __launch_bounds__(TB *(N / P), (65536 / (TB * (N / P) * 128)) > 0 ? 65536 / (TB * (N / P) * 128) : 1)
+filter_step_small_kernel(FilterStepArgs a) {
+  constexpr int T = N / P;
+  constexpr int NT = TB * T;
+  constexpr int WARPS = NT / 32;
+  static_assert(NT % 128 == 0, "whole warpgroups cover the tensor-memory lanes");
+  constexpr uint32_t NCOL = (WARPS / 4) * 64 < 32 ? 32 : (WARPS / 4) * 64;
+  extern __shared__ __align__(128) float2 smem[];
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + TB * N);
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int b = tid / T;
+  const int lt = tid - b * T;
+  float2 *buf = smem + b * N;
+  if (warp == 0) tmem_alloc_warp(tslot, NCOL);
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  const uint32_t tbase = *tslot;
+  const uint32_t taddr = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * (warp >> 2));
+  const uint32_t taddr_x = taddr + 32;
+  {
+    float z[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) z[i] = 0.f;
+    tmem_st16(taddr, z);
+    tmem_st16(taddr + 16, z);
+    tmem_wait_st();
+  }
+  float loss = 0.f;
+  const long long ntiles = (a.batch + TB - 1) / TB;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long next = tile + gridDim.x;
+    if (warp == 0 && next < ntiles) {  // the next tile's x and mask into L2
+      const long long rows = a.batch - next * TB < TB ? a.batch - next * TB : TB;
+      prefetch_l2_warp(a.x + next * TB * N, rows * N * (long long)sizeof(float2), tid);
+      prefetch_l2_warp(a.mask + next * TB * N, rows * N * (long long)sizeof(float), tid);
+    }
+    const long long row = tile * TB + b;
+    const int active = row < a.batch;
+    const long long r0 = active ? row : 0;  // inactive slots compute on zeros, touch nothing
+    loss += step_small_front<N, P, SC>(a.x + r0 * N, active, a.H, a.mask + r0 * N,
+                                       a.y ? a.y + r0 * N : nullptr, buf, a.tw, lt, a.inv_n,
+                                       taddr_x);
+    __syncthreads();  // g_y is in the buffer
+    step_small_back<N, P, SC>(a.gx + r0 * N, active, a.H, buf, a.tw, lt, a.inv_n, taddr, taddr_x);
+    __syncthreads();  // the next tile rewrites the buffer
+  }
+  // the CTA's grad_H row: its TB row slots added in slot order
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    float r[16];
+    tmem_ld16(taddr + 16 * c, r);
+    tmem_wait_ld(r);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) buf[lt + (8 * c + q) * T] = make_float2(r[2 * q], r[2 * q + 1]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
+  tmem_fence_before();
+  __syncthreads();
+  float2 *dst = a.partial + (size_t)blockIdx.x * N;
+  for (int k = tid; k < N; k += NT) {
+    float2 acc = smem[k];
+    for (int t = 1; t < TB; ++t) acc = cadd(acc, smem[t * N + k]);
+    dst[k] = acc;
+  }
+  __syncthreads();  // the slot sums are read: the buffer takes the loss
+  float *red = reinterpret_cast<float *>(smem);
+  if ((tid & 31) == 0) red[warp] = loss;
+  __syncthreads();
+  if (tid == 0) {
+    float t = 0.f;
+    for (int w = 0; w < WARPS; ++w) t += red[w];
+    a.loss_part[blockIdx.x] = t;
+  }
+  if (warp == 0) tmem_dealloc_warp(tbase, NCOL);
+}
+
 // L = the per-CTA loss sums added in a fixed pairwise order (in FP64).
 __global__ void __launch_bounds__(512) loss_tree_kernel(const float *part, int n, float *loss) {
   __shared__ double s[512];
@@ -720,7 +892,10 @@ static FilterVariant variant() {
   }
   if constexpr (P < 32) {
     v.bwd = FilterKernel{nullptr, 0, 0, 0};
-    v.step = FilterKernel{nullptr, 0, 0, 0};
+    v.step.fn = (const void *)&filter_step_small_kernel<N, P, TB, SC>;
+    v.step.threads = TB * (N / P);
+    v.step.tb = TB;
+    v.step.smem = sizeof(float2) * (size_t)N * TB + 16;  // + the tensor-memory address slot
   }
   v.spec = make_kernel<N, P, TB, SC, FM_SPEC>();
   v.mulinv = make_kernel<N, P, TB, SC, FM_MULINV>();
@@ -811,6 +986,25 @@ fft_status_t fft_filter_plan(fft_plan_t *out, int N, int64_t batch) {
   fft_status_t s = build_twiddles(pl, pass_segments(v.sched, off));
   if (s != FFT_OK) return fail(s);
   int64_t work = fft_filter_grad_h_workspace(N, batch);
+  if (!v.bwd.fn && v.step.fn && batch > 0) {
+    // training step of 16-point kernels: resident CTAs as the forward kernel's
+    // occupancy allows, capped by tensor memory (64 columns per group of four
+    // warps) and by the tiles
+    int sms = 0, occ = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v.fwd.fn, v.fwd.threads,
+                                                      v.fwd.smem) != cudaSuccess ||
+        occ < 1)
+      return fail(FFT_ERR_CUDA);
+    const int tmem_cols = std::max(32, (v.step.threads / 128) * 64);
+    const int64_t ntiles = (batch + v.step.tb - 1) / v.step.tb;
+    f->step_grid = (int)std::min<int64_t>((int64_t)std::min(occ, 512 / tmem_cols) * sms, ntiles);
+    work = std::max<int64_t>(work, (int64_t)f->step_grid * N * (int64_t)sizeof(float2));
+    if (dev_malloc(&f->d_loss_part, sizeof(float) * (size_t)f->step_grid) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(FFT_ERR_ALLOC);
+    }
+  }
   if (v.bwd.fn && batch > 0) {
     // Resident CTAs per SM: the occupancy query reports one for any kernel
     // that allocates tensor memory, while the hardware co-schedules as many

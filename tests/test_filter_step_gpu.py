@@ -14,7 +14,7 @@ from gpu_util import NTHREADS, TOL_FP32, TOL_GRAD, rel_l2_rows, to_dev, to_host
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-INVALID_VALUE, NOT_SUPPORTED = 2, 7
+INVALID_VALUE = 2
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -44,9 +44,12 @@ def step(x, H, m, keep_y=True):
 
 
 # 5 and 3 rows: fewer rows than CTAs; 400 and 160: more rows than the
-# resident grid (304 CTAs at 8192, 152 at 16384), so CTAs take 1 or 2 rows
+# resident grid (304 CTAs at 8192, 152 at 16384), so CTAs take 1 or 2 rows.
+# Below 8192 (TB = 4096 / N rows per CTA): one partial tile, and batches of
+# more tiles than resident CTAs with a ragged last tile.
 @pytest.mark.parametrize("rows,N,Np", [(5, 8192, 2048), (400, 8192, 2048), (3, 16384, 4096),
-                                       (160, 16384, 4096)])
+                                       (160, 16384, 4096), (7, 256, 64), (20005, 256, 64),
+                                       (3001, 1024, 256), (1500, 2048, 512), (700, 4096, 1024)])
 def test_fused_step_matches_oracle(rows, N, Np):
     x, H, m = sar_case(rows, N, Np, seed=rows)
     y, loss, gx, gH = step(x, H, m)
@@ -86,11 +89,13 @@ def test_fused_step_at_the_full_config_size():
     assert rel(to_host(layer.H.grad), ogH) <= TOL_GRAD
 
 
-def test_fused_step_agrees_with_the_separate_passes():
-    """y is bitwise the fused forward's (same arithmetic); L, grad_x and
-    grad_H agree with forward + torch's 2 m y + backward to rounding."""
-    rows, N = 64, 8192
-    x, H, m = sar_case(rows, N, 2048, seed=11)
+@pytest.mark.parametrize("N", [1024, 8192])
+def test_fused_step_agrees_with_the_separate_passes(N):
+    """L, grad_x and grad_H agree with forward + torch's 2 m y + backward to
+    rounding; at 8192 y is bitwise the one-kernel forward's (same arithmetic
+    in the same order)."""
+    rows = 64
+    x, H, m = sar_case(rows, N, N // 4, seed=11)
     y, loss, gx, gH = step(x, H, m)
     xd = to_dev(x).requires_grad_(True)
     layer = fg.SpectralFilter(to_dev(H), fused=True)
@@ -98,7 +103,10 @@ def test_fused_step_agrees_with_the_separate_passes():
     ld = (to_dev(m) * (yd.real ** 2 + yd.imag ** 2)).sum()
     ld.backward()
     torch.cuda.synchronize()
-    assert np.array_equal(y.view(np.uint32), to_host(yd.detach()).view(np.uint32))
+    if N == 8192:
+        assert np.array_equal(y.view(np.uint32), to_host(yd.detach()).view(np.uint32))
+    else:
+        assert rel_l2_rows(y, to_host(yd.detach())).max() <= 2e-6
     assert abs(loss - float(ld.detach())) <= 1e-5 * abs(loss)
     assert rel(gx, to_host(xd.grad)) <= 2e-6
     assert rel(gH, to_host(layer.H.grad)) <= 2e-6
@@ -140,13 +148,14 @@ def test_fused_step_edge_cases():
     torch.cuda.synchronize()
     fg.fft_destroy(plan)
     assert float(loss) == 0.0 and not bool(gH.abs().sum())
-    # N without the 32-point kernels: not supported
-    plan = fg.fft_filter_plan(4096, 2)
-    x = torch.zeros(2 * 4096, dtype=torch.complex64, device="cuda")
-    rc = L.fft_filter_step(plan, x.data_ptr(), H.data_ptr(), m.data_ptr(), None, x.data_ptr(),
-                           gH.data_ptr(), loss.data_ptr(), None)
+    # batch 0 at a 16-point size as well
+    plan = fg.fft_filter_plan(1024, 0)
+    gH1 = torch.full((1024,), 3.0 + 1j, dtype=torch.complex64, device="cuda")
+    loss.fill_(5.0)
+    fg.fft_filter_step(plan, buf, H, m, None, buf, gH1, loss, st)
+    torch.cuda.synchronize()
     fg.fft_destroy(plan)
-    assert rc == NOT_SUPPORTED
+    assert float(loss) == 0.0 and not bool(gH1.abs().sum())
     # y overlapping grad_x, and grad_x overlapping the mask: refused
     rows, N = 4, 8192
     plan = fg.fft_filter_plan(N, rows)
